@@ -1,0 +1,181 @@
+/*
+ * j2d5pt.h -- C ABI of the GB300 library for the 2D Jacobi 5-point iterative
+ * stencil (j2d5pt) with deep temporal blocking.
+ *
+ * The operation (Zhang et al., "Exploiting Scratchpad Memory for Deep Temporal
+ * Blocking", GPGPU'23, Section 3.1, Listing 1): for every interior cell
+ *     out[y][x] = W*in[y][x-1] + E*in[y][x+1] + S*in[y-1][x] + C*in[y][x] + N*in[y+1][x]
+ * out of place (Jacobi), iterated for a number of time steps.  The paper moves
+ * the time loop inside the kernel and keeps tiles on chip for several steps
+ * (Sections 3.1 and 3.3, Figure 1); the result does not depend on how the
+ * steps are blocked.  The boundary is a one-cell Dirichlet ring held constant
+ * (the paper is silent on boundaries).
+ *
+ * Array layout ("plan layout").  A grid has nx*ny interior cells plus the
+ * ring: logical cells (y, x) with 0 <= y <= ny+1 and 0 <= x <= nx+1; row 0,
+ * row ny+1, column 0 and column nx+1 are the ring.  Cell (y, x) lives at element
+ *     y * pitch + offset + x
+ * of a device buffer of (ny+2) * pitch elements, where pitch and offset come
+ * from j2d5pt_layout().  The offset puts interior column 1 on a 16-byte
+ * boundary; pitch * sizeof(element) is a multiple of 16.  Elements outside the
+ * logical array (the `offset` leading elements of each row and the tail
+ * padding) are never read; the library may overwrite them in output arrays.
+ * Buffers must be 16-byte aligned (cudaMalloc gives 256).  Inputs must be
+ * finite.
+ *
+ * Ownership.  All data buffers are owned by the caller; the library never
+ * frees them.  A plan owns its device workspace, freed by
+ * j2d5pt_plan_destroy().  Plans are not thread safe; use one plan per thread.
+ *
+ * Streams and errors.  Run calls are asynchronous on the given CUDA stream
+ * (a cudaStream_t passed as void*, NULL = legacy default stream); argument
+ * errors are returned synchronously and nothing is enqueued.  Device-side
+ * errors (a wait that timed out, a failed bound check) are recorded in the
+ * plan and reported by j2d5pt_sync_status(), which synchronises the stream of
+ * the last run.  j2d5pt_last_error() gives a message for the most recent
+ * failure on the calling thread.
+ */
+#ifndef J2D5PT_H
+#define J2D5PT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct j2d5pt_plan_s *j2d5pt_plan_t;
+
+typedef enum { J2D_F64 = 0, J2D_F32 = 1 } j2d_dtype;
+
+typedef enum {
+  J2D_OK = 0,
+  J2D_ERR_ARG = 1,         /* invalid argument (null pointer, size, step count) */
+  J2D_ERR_ALIGN = 2,       /* buffer not 16-byte aligned */
+  J2D_ERR_NOMEM = 3,       /* workspace allocation failed */
+  J2D_ERR_DEVICE = 4,      /* CUDA runtime error */
+  J2D_ERR_UNSUPPORTED = 5, /* configuration not available on this device */
+  J2D_ERR_TIMEOUT = 6,     /* a device-side wait gave up; results are invalid */
+  J2D_ERR_BOUNDS = 7       /* a device-side bound check failed */
+} j2d_status;
+
+/* Kernel families a plan can run.  AUTO uses the plan's tuned or heuristic choice. */
+typedef enum {
+  J2D_ALGO_AUTO = 0,
+  J2D_ALGO_ONESTEP = 1,  /* one launch per time step, streaming through HBM */
+  J2D_ALGO_RESIDENT = 2, /* whole grid held on chip for all steps; one persistent launch */
+  J2D_ALGO_BANDS = 3,    /* GPU-wide bands of the grid, processed serially, k steps per visit */
+  J2D_ALGO_TILES = 4     /* independent per-CTA tiles with a k-deep overlapped halo */
+} j2d_algo;
+
+/* Plan options (j2d5pt_set_option / j2d5pt_get_option). */
+typedef enum {
+  J2D_OPT_ALGO = 0,       /* j2d_algo */
+  J2D_OPT_DEPTH = 1,      /* temporal depth k (steps per on-chip visit) for BANDS / TILES */
+  J2D_OPT_TILE_WX = 2,    /* TILES: warp strips across a CTA tile (16 / WX down) */
+  J2D_OPT_CTAS = 3,       /* persistent grid size (0 = one CTA per SM) */
+  J2D_OPT_TIMEOUT_MS = 4, /* device-side wait limit in milliseconds (default 2000) */
+  J2D_OPT_VERBOSE = 5     /* 1 = print the chosen configuration to stderr at run time */
+} j2d_option;
+
+/* ---- plans ------------------------------------------------------------- */
+
+/* Plan for one grid of nx*ny interior cells.  weights = {W, E, S, C, N} (host,
+ * FP64; rounded to float for J2D_F32 plans; used as given, not normalised).
+ * Queries the current CUDA device and allocates the plan's workspace on it. */
+j2d_status j2d5pt_plan(j2d5pt_plan_t *plan, int nx, int ny, j2d_dtype dtype,
+                       const double weights[5]);
+
+/* Plan for `count` independent grids advanced together (one persistent launch).
+ * nx[i], ny[i]: interior sizes; weights: count*5 values, grid i at weights+5*i. */
+j2d_status j2d5pt_plan_batched(j2d5pt_plan_t *plan, int count, const int *nx, const int *ny,
+                               j2d_dtype dtype, const double *weights);
+
+j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t plan);
+
+/* Layout of grid `index` (0 for single-grid plans): elements per row and the
+ * element offset of logical column 0 (see the layout rules above). */
+j2d_status j2d5pt_layout(j2d5pt_plan_t plan, int index, long *pitch, long *offset);
+
+j2d_status j2d5pt_set_option(j2d5pt_plan_t plan, j2d_option opt, long value);
+j2d_status j2d5pt_get_option(j2d5pt_plan_t plan, j2d_option opt, long *value);
+
+/* Human-readable description of the configuration the next run will use. */
+j2d_status j2d5pt_describe(j2d5pt_plan_t plan, char *buf, size_t len);
+
+/* ---- forward ----------------------------------------------------------- */
+
+/* u_steps = M^steps u_0 (Section 3.1's update applied `steps` times, ring held
+ * constant).  in, out: device buffers in plan layout; they may alias.
+ * steps = 0 copies.  Asynchronous on `stream`. */
+j2d_status j2d5pt_run(j2d5pt_plan_t plan, const void *in, void *out, long steps, void *stream);
+
+/* Same, for a batched plan: in[i], out[i] (host arrays of device pointers) are
+ * grid i's buffers in its own layout. */
+j2d_status j2d5pt_run_batched(j2d5pt_plan_t plan, const void *const *in, void *const *out,
+                              long steps, void *stream);
+
+/* End-to-end form on HOST buffers: h_in and h_out are dense (ny+2) x (nx+2)
+ * row-major host arrays (ring included).  Copies in, runs, copies out and
+ * synchronises; uses the plan's device workspace.  Pinned host memory gives
+ * full copy bandwidth. */
+j2d_status j2d5pt_run_host(j2d5pt_plan_t plan, const void *h_in, void *h_out, long steps);
+
+/* ---- adjoint and gradient (the transpose of the forward map) ------------ */
+
+/* lam_0 = (M^T)^steps lam_T, where M is one forward step over all cells
+ * (interior rows of M hold the five weights, ring rows are the identity).
+ * Interior cells follow the transposed stencil with weights mirrored
+ * (x-1 <- E, x+1 <- W, y-1 <- N, y+1 <- S) and reading only interior cells;
+ * ring cells keep their value and add the weight of their link times the
+ * adjacent interior value each step; corners are unchanged.  Buffers in plan
+ * layout; they may alias. */
+j2d_status j2d5pt_run_adjoint(j2d5pt_plan_t plan, const void *lam_T, void *lam_0, long steps,
+                              void *stream);
+
+/* dw[d] += sum over interior cells i of lam_t1[i] * u_t[nbr_d(i)], d = W, E, S,
+ * C, N (nbr = x-1, x+1, y-1, self, y+1): the gradient contribution of one
+ * step t of L = <g, u_T> with lam_t1 = (M^T)^(T-t-1) g.  dw: 5 doubles in
+ * device memory, accumulated (not overwritten).  The sum is reduced in a
+ * fixed order, so results are reproducible. */
+j2d_status j2d5pt_weight_grad(j2d5pt_plan_t plan, const void *u_t, const void *lam_t1,
+                              double *dw, void *stream);
+
+/* ---- status, tuning, diagnostics ---------------------------------------- */
+
+/* Synchronise the stream of the plan's last run and return its device-side
+ * status (J2D_OK, J2D_ERR_TIMEOUT, J2D_ERR_BOUNDS) or a CUDA error; clears it. */
+j2d_status j2d5pt_sync_status(j2d5pt_plan_t plan);
+
+/* Time the candidate configurations for `steps` steps on the given buffers
+ * (out is overwritten; in is only read unless in == out) and keep the fastest
+ * in the plan.  Results are cached in the file named by J2D_TUNE_CACHE if set.
+ * Synchronous. */
+j2d_status j2d5pt_autotune(j2d5pt_plan_t plan, const void *in, void *out, long steps,
+                           void *stream);
+
+/* Same for a batched plan (in[i], out[i] as for j2d5pt_run_batched); picks the
+ * temporal depth and tile shape of the batched kernel. */
+j2d_status j2d5pt_autotune_batched(j2d5pt_plan_t plan, const void *const *in, void *const *out,
+                                   long steps, void *stream);
+
+/* Measured fused multiply-add throughput of the current device for `dtype`
+ * (FMA instructions per second), from a short dependent-free FMA loop.  Used
+ * as the arithmetic roofline. Synchronous. */
+j2d_status j2d5pt_measure_fma_rate(j2d_dtype dtype, double *fma_per_s);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all plans); a diagnostic for launch accounting. */
+long j2d5pt_kernel_launches(void);
+
+/* Message for the most recent failing call on this thread ("" if none). */
+const char *j2d5pt_last_error(void);
+
+/* Library version string. */
+const char *j2d5pt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* J2D5PT_H */

@@ -1,0 +1,503 @@
+// api.cu -- the C ABI (include/j2d5pt.h): plans, validation, workspace,
+// dispatch to the one-step and temporally blocked kernels, host end-to-end
+// runs, status reporting.
+#include <cmath>
+#include <cstdint>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dtb.h"
+#include "internal.h"
+
+using namespace j2d;
+
+static thread_local std::string g_last_error;
+
+static j2d_status fail(j2d_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+static j2d_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(J2D_ERR_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct j2d5pt_plan_s {
+  int device = 0;
+  j2d_dtype dtype = J2D_F64;
+  size_t elem = 8;
+  std::vector<GridDesc> grids;
+  // options
+  int opt_algo = J2D_ALGO_AUTO, opt_depth = 0, opt_tile_wx = 0, opt_ctas = 0, opt_verbose = 0;
+  int opt_timeout_ms = 2000;
+  // device info
+  int sms = 0;
+  size_t smem_optin = 0;
+  // workspace: one extra buffer per grid (ping-pong), weight-gradient partials, status word
+  void *ws = nullptr;
+  std::vector<size_t> ws_off;
+  double *partials = nullptr;
+  int *d_status = nullptr;
+  // host end-to-end staging (device buffers), allocated on first use
+  void *h_in_dev = nullptr, *h_out_dev = nullptr;
+  // scratch of the temporally blocked kernels
+  DtbState dtb;
+  cudaStream_t last_stream = nullptr;
+  bool ran = false;
+};
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static j2d_status plan_common(j2d5pt_plan_t *out, int count, const int *nx, const int *ny, j2d_dtype dt,
+                              const double *w) {
+  if (!out) return fail(J2D_ERR_ARG, "plan: null output pointer");
+  *out = nullptr;
+  if (dt != J2D_F64 && dt != J2D_F32) return fail(J2D_ERR_ARG, "plan: unknown dtype %d", (int)dt);
+  if (count < 1 || !nx || !ny || !w) return fail(J2D_ERR_ARG, "plan: need count >= 1 and non-null sizes/weights");
+  for (int i = 0; i < count; ++i) {
+    if (nx[i] < 1 || ny[i] < 1) return fail(J2D_ERR_ARG, "plan: grid %d has nx=%d ny=%d (need >= 1)", i, nx[i], ny[i]);
+    if ((long)nx[i] + 8 > (1L << 30) || (long)ny[i] + 8 > (1L << 30))
+      return fail(J2D_ERR_ARG, "plan: grid %d too large", i);
+    for (int d = 0; d < 5; ++d)
+      if (!std::isfinite(w[5 * i + d])) return fail(J2D_ERR_ARG, "plan: grid %d weight %d is not finite", i, d);
+  }
+  auto *p = new j2d5pt_plan_s();
+  p->dtype = dt;
+  p->elem = dt == J2D_F64 ? 8 : 4;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) { delete p; return cuda_fail(e, "plan: cudaGetDevice"); }
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, p->device)) != cudaSuccess) { delete p; return cuda_fail(e, "plan: properties"); }
+  p->sms = prop.multiProcessorCount;
+  p->smem_optin = prop.sharedMemPerBlockOptin;
+  const long vec = 16 / (long)p->elem;
+  size_t ws_bytes = 0;
+  long max_partials = 0;
+  for (int i = 0; i < count; ++i) {
+    GridDesc g;
+    g.nx = nx[i];
+    g.ny = ny[i];
+    g.off = vec - 1;
+    g.pitch = ((g.off + g.nx + 2) + vec - 1) / vec * vec;
+    for (int d = 0; d < 5; ++d) g.w[d] = dt == J2D_F64 ? w[5 * i + d] : (double)(float)w[5 * i + d];
+    p->grids.push_back(g);
+    p->ws_off.push_back(ws_bytes);
+    ws_bytes += (g.bytes(p->elem) + 255) / 256 * 256;
+    long np = wgrad_partial_count(dt, g);
+    if (np > max_partials) max_partials = np;
+  }
+  if ((e = cudaMalloc(&p->ws, ws_bytes)) != cudaSuccess) { delete p; return fail(J2D_ERR_NOMEM, "plan: workspace of %zu bytes: %s", ws_bytes, cudaGetErrorString(e)); }
+  if ((e = cudaMalloc(&p->partials, sizeof(double) * 5 * (size_t)max_partials + 64)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_status, 64)) != cudaSuccess || (e = cudaMemset(p->d_status, 0, 64)) != cudaSuccess) {
+    cudaFree(p->ws);
+    cudaFree(p->partials);
+    cudaFree(p->d_status);
+    delete p;
+    return fail(J2D_ERR_NOMEM, "plan: small buffers: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  g_last_error.clear();
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_plan(j2d5pt_plan_t *plan, int nx, int ny, j2d_dtype dtype, const double weights[5]) {
+  return plan_common(plan, 1, &nx, &ny, dtype, weights);
+}
+
+extern "C" j2d_status j2d5pt_plan_batched(j2d5pt_plan_t *plan, int count, const int *nx, const int *ny,
+                                          j2d_dtype dtype, const double *weights) {
+  return plan_common(plan, count, nx, ny, dtype, weights);
+}
+
+extern "C" j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t p) {
+  if (!p) return fail(J2D_ERR_ARG, "destroy: null plan");
+  if (p->ran && p->last_stream) cudaStreamSynchronize(p->last_stream);
+  dtb_release(p->dtb);
+  cudaFree(p->ws);
+  cudaFree(p->partials);
+  cudaFree(p->d_status);
+  cudaFree(p->h_in_dev);
+  cudaFree(p->h_out_dev);
+  delete p;
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_layout(j2d5pt_plan_t p, int index, long *pitch, long *offset) {
+  if (!p) return fail(J2D_ERR_ARG, "layout: null plan");
+  if (index < 0 || index >= (int)p->grids.size()) return fail(J2D_ERR_ARG, "layout: index %d out of range", index);
+  if (pitch) *pitch = p->grids[index].pitch;
+  if (offset) *offset = p->grids[index].off;
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v) {
+  if (!p) return fail(J2D_ERR_ARG, "set_option: null plan");
+  switch (opt) {
+    case J2D_OPT_ALGO:
+      if (v < J2D_ALGO_AUTO || v > J2D_ALGO_TILES) return fail(J2D_ERR_ARG, "set_option: bad algo %ld", v);
+      p->opt_algo = (int)v;
+      break;
+    case J2D_OPT_DEPTH:
+      if (v < 0 || v > 256) return fail(J2D_ERR_ARG, "set_option: depth %ld outside 0..256", v);
+      p->opt_depth = (int)v;
+      break;
+    case J2D_OPT_TILE_WX:
+      if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8 && v != 16)
+        return fail(J2D_ERR_ARG, "set_option: tile_wx must be 0, 1, 2, 4, 8 or 16");
+      p->opt_tile_wx = (int)v;
+      break;
+    case J2D_OPT_CTAS:
+      if (v < 0 || v > 65535) return fail(J2D_ERR_ARG, "set_option: ctas %ld", v);
+      p->opt_ctas = (int)v;
+      break;
+    case J2D_OPT_TIMEOUT_MS:
+      if (v < 1 || v > 600000) return fail(J2D_ERR_ARG, "set_option: timeout %ld ms", v);
+      p->opt_timeout_ms = (int)v;
+      break;
+    case J2D_OPT_VERBOSE:
+      p->opt_verbose = (int)v;
+      break;
+    default:
+      return fail(J2D_ERR_ARG, "set_option: unknown option %d", (int)opt);
+  }
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_get_option(j2d5pt_plan_t p, j2d_option opt, long *v) {
+  if (!p || !v) return fail(J2D_ERR_ARG, "get_option: null argument");
+  switch (opt) {
+    case J2D_OPT_ALGO: *v = p->opt_algo; break;
+    case J2D_OPT_DEPTH: *v = p->opt_depth; break;
+    case J2D_OPT_TILE_WX: *v = p->opt_tile_wx; break;
+    case J2D_OPT_CTAS: *v = p->opt_ctas; break;
+    case J2D_OPT_TIMEOUT_MS: *v = p->opt_timeout_ms; break;
+    case J2D_OPT_VERBOSE: *v = p->opt_verbose; break;
+    default: return fail(J2D_ERR_ARG, "get_option: unknown option %d", (int)opt);
+  }
+  return J2D_OK;
+}
+
+// Resolve the configuration a run will use.
+static DtbConfig resolve(j2d5pt_plan_t p, long steps, bool adj) {
+  DtbRequest rq;
+  rq.algo = p->opt_algo;
+  rq.depth = p->opt_depth;
+  rq.tile_wx = p->opt_tile_wx;
+  rq.ctas = p->opt_ctas;
+  rq.steps = steps;
+  rq.adjoint = adj;
+  return dtb_choose(p->dtype, p->grids, p->sms, p->smem_optin, rq);
+}
+
+static const char *algo_name(int a) {
+  switch (a) {
+    case J2D_ALGO_ONESTEP: return "onestep";
+    case J2D_ALGO_RESIDENT: return "resident";
+    case J2D_ALGO_BANDS: return "bands";
+    case J2D_ALGO_TILES: return "tiles";
+    default: return "auto";
+  }
+}
+
+extern "C" j2d_status j2d5pt_describe(j2d5pt_plan_t p, char *buf, size_t len) {
+  if (!p || !buf || len == 0) return fail(J2D_ERR_ARG, "describe: null argument");
+  DtbConfig c = resolve(p, 1000, false);
+  snprintf(buf, len, "dtype=%s grids=%zu nx=%d ny=%d pitch=%ld offset=%ld algo=%s depth=%d tile_wx=%d ctas=%d rows=%d sms=%d",
+           p->dtype == J2D_F64 ? "f64" : "f32", p->grids.size(), p->grids[0].nx, p->grids[0].ny, p->grids[0].pitch,
+           p->grids[0].off, algo_name(c.algo), c.depth, c.tile_wx, c.ctas, c.rows, p->sms);
+  return J2D_OK;
+}
+
+static char *ws_of(j2d5pt_plan_t p, int i) { return (char *)p->ws + p->ws_off[i]; }
+
+// One grid, `steps` forward (or adjoint) steps, in -> out.
+static j2d_status run_grid_onestep(j2d5pt_plan_t p, int gi, const void *in, void *out, long steps, bool adj,
+                                   cudaStream_t s) {
+  const GridDesc &g = p->grids[gi];
+  const size_t bytes = g.bytes(p->elem);
+  cudaError_t e;
+  if (steps == 0) {
+    if (in != out && (e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "run: copy");
+    return J2D_OK;
+  }
+  void *ws = ws_of(p, gi);
+  const void *src = in;
+  if (in == out && (steps & 1)) {
+    if ((e = cudaMemcpyAsync(ws, in, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return cuda_fail(e, "run: copy");
+    src = ws;
+  }
+  for (long t = 0; t < steps; ++t) {
+    void *dst = ((steps - 1 - t) % 2 == 0) ? out : ws;
+    if ((e = launch_onestep(p->dtype, adj, src, dst, g, s)) != cudaSuccess) return cuda_fail(e, "run: one-step launch");
+    src = dst;
+  }
+  return J2D_OK;
+}
+
+static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps, bool adj,
+                             cudaStream_t s) {
+  if (steps < 0) return fail(J2D_ERR_ARG, "run: steps %ld < 0", steps);
+  for (size_t i = 0; i < p->grids.size(); ++i) {
+    if (!in[i] || !out[i]) return fail(J2D_ERR_ARG, "run: null buffer for grid %zu", i);
+    if (!aligned16(in[i]) || !aligned16(out[i])) return fail(J2D_ERR_ALIGN, "run: buffer for grid %zu not 16-byte aligned", i);
+  }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != p->device) return fail(J2D_ERR_DEVICE, "run: current device %d differs from the plan's device %d", cur, p->device);
+  DtbConfig c = resolve(p, steps, adj);
+  if (p->opt_verbose)
+    fprintf(stderr, "[j2d5pt] run steps=%ld adj=%d algo=%s depth=%d tile_wx=%d ctas=%d rows=%d\n", steps, (int)adj,
+            algo_name(c.algo), c.depth, c.tile_wx, c.ctas, c.rows);
+  p->last_stream = s;
+  p->ran = true;
+  if (c.algo == J2D_ALGO_ONESTEP || steps == 0) {
+    for (size_t i = 0; i < p->grids.size(); ++i) {
+      j2d_status st = run_grid_onestep(p, (int)i, in[i], out[i], steps, adj, s);
+      if (st != J2D_OK) return st;
+    }
+    return J2D_OK;
+  }
+  std::vector<void *> wsv;
+  for (size_t i = 0; i < p->grids.size(); ++i) wsv.push_back(ws_of(p, (int)i));
+  DtbRun r;
+  r.dtype = p->dtype;
+  r.grids = &p->grids;
+  r.in = in;
+  r.out = out;
+  r.ws = wsv.data();
+  r.steps = steps;
+  r.adjoint = adj;
+  r.cfg = c;
+  r.status = p->d_status;
+  r.timeout_ns = (unsigned long long)p->opt_timeout_ms * 1000000ull;
+  r.sms = p->sms;
+  r.smem_optin = p->smem_optin;
+  std::string err;
+  cudaError_t e = dtb_run(p->dtb, r, s, err);
+  if (e == cudaErrorNotSupported) return fail(J2D_ERR_UNSUPPORTED, "run: %s", err.c_str());
+  if (e == cudaErrorMemoryAllocation) return fail(J2D_ERR_NOMEM, "run: %s", err.c_str());
+  if (e != cudaSuccess) return fail(J2D_ERR_DEVICE, "run: %s: %s", err.c_str(), cudaGetErrorString(e));
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_run(j2d5pt_plan_t p, const void *in, void *out, long steps, void *stream) {
+  if (!p) return fail(J2D_ERR_ARG, "run: null plan");
+  if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "run: batched plan; use j2d5pt_run_batched");
+  return run_common(p, &in, &out, steps, false, (cudaStream_t)stream);
+}
+
+extern "C" j2d_status j2d5pt_run_batched(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps,
+                                         void *stream) {
+  if (!p || !in || !out) return fail(J2D_ERR_ARG, "run_batched: null argument");
+  return run_common(p, in, out, steps, false, (cudaStream_t)stream);
+}
+
+extern "C" j2d_status j2d5pt_run_adjoint(j2d5pt_plan_t p, const void *lam_T, void *lam_0, long steps, void *stream) {
+  if (!p) return fail(J2D_ERR_ARG, "run_adjoint: null plan");
+  if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "run_adjoint: batched plans are forward only");
+  return run_common(p, &lam_T, &lam_0, steps, true, (cudaStream_t)stream);
+}
+
+extern "C" j2d_status j2d5pt_weight_grad(j2d5pt_plan_t p, const void *u_t, const void *lam_t1, double *dw,
+                                         void *stream) {
+  if (!p || !u_t || !lam_t1 || !dw) return fail(J2D_ERR_ARG, "weight_grad: null argument");
+  if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "weight_grad: batched plans are forward only");
+  if (!aligned16(u_t) || !aligned16(lam_t1)) return fail(J2D_ERR_ALIGN, "weight_grad: buffer not 16-byte aligned");
+  if (((uintptr_t)dw & 7u) != 0) return fail(J2D_ERR_ALIGN, "weight_grad: dw not 8-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  p->ran = true;
+  cudaError_t e = launch_wgrad(p->dtype, u_t, lam_t1, dw, p->partials, p->grids[0], s);
+  if (e != cudaSuccess) return cuda_fail(e, "weight_grad: launch");
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_run_host(j2d5pt_plan_t p, const void *h_in, void *h_out, long steps) {
+  if (!p || !h_in || !h_out) return fail(J2D_ERR_ARG, "run_host: null argument");
+  if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "run_host: single-grid plans only");
+  const GridDesc &g = p->grids[0];
+  cudaError_t e;
+  if (!p->h_in_dev) {
+    if ((e = cudaMalloc(&p->h_in_dev, g.bytes(p->elem))) != cudaSuccess ||
+        (e = cudaMalloc(&p->h_out_dev, g.bytes(p->elem))) != cudaSuccess) {
+      cudaFree(p->h_in_dev);
+      p->h_in_dev = nullptr;
+      return fail(J2D_ERR_NOMEM, "run_host: staging buffers: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaStream_t s = nullptr;
+  const size_t w = (size_t)(g.nx + 2) * p->elem, dp = (size_t)g.pitch * p->elem;
+  char *din = (char *)p->h_in_dev + g.off * p->elem, *dout = (char *)p->h_out_dev + g.off * p->elem;
+  if ((e = cudaMemcpy2DAsync(din, dp, h_in, w, w, g.ny + 2, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "run_host: copy in");
+  j2d_status st = j2d5pt_run(p, p->h_in_dev, p->h_out_dev, steps, s);
+  if (st != J2D_OK) return st;
+  if ((e = cudaMemcpy2DAsync(h_out, w, dout, dp, w, g.ny + 2, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "run_host: copy out");
+  return j2d5pt_sync_status(p);
+}
+
+extern "C" j2d_status j2d5pt_sync_status(j2d5pt_plan_t p) {
+  if (!p) return fail(J2D_ERR_ARG, "sync_status: null plan");
+  cudaError_t e = p->ran ? cudaStreamSynchronize(p->last_stream) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "sync_status: stream");
+  int st = 0;
+  if ((e = cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "sync_status: read");
+  if (st != 0) {
+    cudaMemset(p->d_status, 0, sizeof(int));
+    if (st == J2D_ERR_TIMEOUT) return fail(J2D_ERR_TIMEOUT, "device: a wait exceeded the time limit; results invalid");
+    return fail((j2d_status)st, "device: bound check failed (code %d); results invalid", st);
+  }
+  return J2D_OK;
+}
+
+// Autotuner.  Candidates: the one-step kernel; the resident kernel when the
+// grid fits on chip; bands and tiles over temporal depths k (and tile shapes).
+// Each is timed with CUDA events for min(steps, 64) steps after one warm-up
+// run; the fastest is kept in the plan.  With J2D_TUNE_CACHE set, results are
+// read from / appended to that file, keyed by device, SM count, dtype, grid
+// sizes and the step-count bucket.
+static std::string tune_key(j2d5pt_plan_t p, long steps) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, p->device);
+  std::string k = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) + "|" +
+                  (p->dtype == J2D_F64 ? "f64" : "f32");
+  unsigned long long h = 1469598103934665603ull;
+  for (const GridDesc &g : p->grids) {
+    h = (h ^ (unsigned long long)g.nx) * 1099511628211ull;
+    h = (h ^ (unsigned long long)g.ny) * 1099511628211ull;
+  }
+  k += "|" + std::to_string(p->grids.size()) + "|" + std::to_string(h);
+  long b = 1;
+  while (b < steps) b <<= 1;
+  k += "|" + std::to_string(b);
+  return k;
+}
+
+static bool tune_cache_lookup(const std::string &key, int *algo, int *depth, int *wx) {
+  const char *path = getenv("J2D_TUNE_CACHE");
+  if (!path) return false;
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    char k[400];
+    int a, d, w;
+    if (sscanf(line, "%399s %d %d %d", k, &a, &d, &w) == 4 && key == k) {
+      *algo = a; *depth = d; *wx = w;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+static void tune_cache_store(const std::string &key, int algo, int depth, int wx) {
+  const char *path = getenv("J2D_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d\n", key.c_str(), algo, depth, wx);
+  fclose(f);
+}
+
+static j2d_status autotune_common(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps,
+                                  cudaStream_t s) {
+  std::string key = tune_key(p, steps);
+  int ca, cd, cw;
+  if (tune_cache_lookup(key, &ca, &cd, &cw)) {
+    p->opt_algo = ca;
+    p->opt_depth = cd;
+    p->opt_tile_wx = cw;
+    return J2D_OK;
+  }
+  struct Cand { int algo, depth, wx; };
+  std::vector<Cand> cands;
+  const long tsteps = std::min<long>(steps, 64);
+  const bool single = p->grids.size() == 1;
+  if (single) cands.push_back({J2D_ALGO_ONESTEP, 0, 0});
+  {
+    DtbRequest rq;
+    rq.algo = J2D_ALGO_RESIDENT;
+    rq.steps = steps;
+    if (single && dtb_choose(p->dtype, p->grids, p->sms, p->smem_optin, rq).algo == J2D_ALGO_RESIDENT)
+      cands.push_back({J2D_ALGO_RESIDENT, 0, 0});
+  }
+  const int depths[] = {2, 4, 6, 8, 12, 16, 24, 32};
+  for (int d : depths) {
+    if (d > steps) break;
+    if (single) cands.push_back({J2D_ALGO_BANDS, d, 0});
+    for (int wx : {1, 2, 4}) cands.push_back({J2D_ALGO_TILES, d, wx});
+  }
+  float best_ms = 1e30f;
+  Cand best = {J2D_ALGO_AUTO, 0, 0};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (const Cand &c : cands) {
+    p->opt_algo = c.algo;
+    p->opt_depth = c.depth;
+    p->opt_tile_wx = c.wx;
+    if (run_common(p, in, out, tsteps, false, s) != J2D_OK || j2d5pt_sync_status(p) != J2D_OK) continue;
+    cudaEventRecord(e0, s);
+    j2d_status st = run_common(p, in, out, tsteps, false, s);
+    cudaEventRecord(e1, s);
+    if (st != J2D_OK || cudaEventSynchronize(e1) != cudaSuccess || j2d5pt_sync_status(p) != J2D_OK) continue;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (p->opt_verbose)
+      fprintf(stderr, "[j2d5pt] tune algo=%d depth=%d wx=%d: %.3f ms for %ld steps\n", c.algo, c.depth, c.wx, ms,
+              tsteps);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->opt_algo = best.algo;
+  p->opt_depth = best.depth;
+  p->opt_tile_wx = best.wx;
+  tune_cache_store(key, best.algo, best.depth, best.wx);
+  g_last_error.clear();
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_autotune(j2d5pt_plan_t p, const void *in, void *out, long steps, void *stream) {
+  if (!p || !in || !out) return fail(J2D_ERR_ARG, "autotune: null argument");
+  if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "autotune: batched plan; use j2d5pt_autotune_batched");
+  if (steps < 1) return fail(J2D_ERR_ARG, "autotune: steps must be >= 1");
+  return autotune_common(p, &in, &out, steps, (cudaStream_t)stream);
+}
+
+extern "C" j2d_status j2d5pt_autotune_batched(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps,
+                                              void *stream) {
+  if (!p || !in || !out) return fail(J2D_ERR_ARG, "autotune_batched: null argument");
+  if (steps < 1) return fail(J2D_ERR_ARG, "autotune_batched: steps must be >= 1");
+  return autotune_common(p, in, out, steps, (cudaStream_t)stream);
+}
+
+extern "C" j2d_status j2d5pt_measure_fma_rate(j2d_dtype dt, double *rate) {
+  if (!rate || (dt != J2D_F64 && dt != J2D_F32)) return fail(J2D_ERR_ARG, "measure_fma_rate: bad argument");
+  cudaError_t e = measure_fma(dt, rate);
+  if (e != cudaSuccess) return cuda_fail(e, "measure_fma_rate");
+  return J2D_OK;
+}
+
+extern "C" long j2d5pt_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" const char *j2d5pt_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *j2d5pt_version(void) { return "j2d5pt-gb300 0.1 (sm_103a)"; }

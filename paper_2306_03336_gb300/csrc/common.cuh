@@ -1,0 +1,157 @@
+// common.cuh -- device helpers shared by the j2d5pt kernels (sm_103a).
+//
+// The stencil (Zhang et al., GPGPU'23, Section 3.1, Listing 1) updates a cell
+// from its x-1, x+1, y-1, centre and y+1 neighbours with weights W, E, S, C, N.
+// Every kernel here evaluates it as one product followed by four fused
+// multiply-adds in that operand order, so the one-step kernel and the
+// temporally blocked kernels give bit-identical results for the same inputs.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace j2d {
+
+// Device-side status codes (mirrors of j2d_status values).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 6, DEV_BOUNDS = 7 };
+
+// Elements per 16-byte vector: 2 doubles or 4 floats.
+template <typename T> struct VecOf;
+template <> struct VecOf<double> { static constexpr int V = 2; using type = double2; };
+template <> struct VecOf<float> { static constexpr int V = 4; using type = float4; };
+
+// The five link weights of one cell: x-1, x+1, y-1, centre, y+1.
+template <typename T> struct Links { T xm, xp, ym, c, yp; };
+
+// Base weights as the user gives them: W (x-1), E (x+1), S (y-1), C, N (y+1).
+template <typename T> struct Weights { T w[5]; };
+
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// One cell update: product of the x-1 link, then fused multiply-adds of the
+// x+1, y-1, centre and y+1 links (the operand order of Listing 1).
+template <typename T>
+__device__ __forceinline__ T stencil(const Links<T> &a, T xm, T xp, T ym, T c, T yp) {
+  T r = mul_rn(a.xm, xm);
+  r = fma_rn(a.xp, xp, r);
+  r = fma_rn(a.ym, ym, r);
+  r = fma_rn(a.c, c, r);
+  r = fma_rn(a.yp, yp, r);
+  return r;
+}
+
+// Link weights of logical cell (x, y) of an nx*ny grid with a one-cell ring.
+// Forward: interior cells use W, E, S, C, N; ring and outside cells keep their
+// value (identity).  Adjoint (the transpose of one forward step): interior
+// cells use the mirrored weights with links to ring cells removed; a ring cell
+// keeps its value and adds its one interior neighbour times the weight of
+// the forward link that read it; corners and outside cells keep their value.
+template <typename T, bool ADJ>
+__device__ __forceinline__ Links<T> cell_links(int x, int y, int nx, int ny, const Weights<T> &w) {
+  const T W = w.w[0], E = w.w[1], S = w.w[2], C = w.w[3], N = w.w[4];
+  const T z = T(0), one = T(1);
+  const bool xi = (x >= 1) && (x <= nx), yi = (y >= 1) && (y <= ny);
+  if (!ADJ) {
+    if (xi && yi) return {W, E, S, C, N};
+    return {z, z, z, one, z};
+  }
+  if (xi && yi) return {x >= 2 ? E : z, x <= nx - 1 ? W : z, y >= 2 ? N : z, C, y <= ny - 1 ? S : z};
+  if (yi && x == 0) return {z, W, z, one, z};
+  if (yi && x == nx + 1) return {E, z, z, one, z};
+  if (xi && y == 0) return {z, z, z, one, S};
+  if (xi && y == ny + 1) return {z, z, N, one, z};
+  return {z, z, z, one, z};
+}
+
+// ---- small PTX wrappers ----------------------------------------------------
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(int *p, int v) {
+  asm volatile("st.relaxed.gpu.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta(const int *p) {
+  int v;
+  asm volatile("ld.acquire.cta.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_cta(int *p, int v) {
+  asm volatile("st.relaxed.cta.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_acq_rel_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
+
+// Global loads that bypass L1 (halo mailboxes written by other SMs).
+__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// mbarrier (shared memory transaction barrier) for TMA completion.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// 2D tiled TMA load: box at (x, y) of the tensor map into shared memory,
+// completing on `bar` with the box's byte count.
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const void *tmap, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// 2D tiled TMA store from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const void *tmap, int x, int y, const void *smem_src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(tmap),
+               "r"(x), "r"(y), "r"(smem_u32(smem_src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Record the first device-side error of a run; later errors are dropped.
+__device__ __forceinline__ void set_error(int *status, int code) {
+  if (status) atomicCAS(status, DEV_OK, code);
+}
+__device__ __forceinline__ bool has_error(const int *status) {
+  return status && *((volatile const int *)status) != DEV_OK;
+}
+
+}  // namespace j2d

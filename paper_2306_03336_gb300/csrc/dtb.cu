@@ -1,0 +1,886 @@
+// dtb.cu -- deep temporal blocking (DTB) kernels for j2d5pt on sm_103a.
+//
+// The method (Zhang et al., GPGPU'23, Sections 3.1-3.3, Figure 1): tile the
+// domain so that a tile fills the GPU's shared memory, load it once, advance
+// it several time steps on chip with device-wide synchronisation resolving
+// the halos between thread blocks, then store it; tiles are processed one
+// after another.  The paper's step function (Listing 1) is the same whether
+// its pointers address global or shared memory.
+//
+// GB300 design.  The unit of work is a warp-owned *strip*: 32 lanes x one
+// 16-byte vector each (64 FP64 or 128 FP32 columns) by up to R rows, held in
+// the CTA's shared memory.  A warp sweeps its strip row by row with a
+// three-row register window (the listing's column cache), exchanges the x+-1
+// neighbours across lanes with shuffles, and updates the strip in place.
+// Halos between strips are point to point: at the end of every step a strip
+// writes its four edges into double-buffered mailboxes of its neighbours
+// (shared memory when the neighbour is in the same CTA, L2-resident global
+// memory otherwise) and publishes a per-warp step counter; a strip waits only
+// for its own (at most four) neighbours' counters.  This replaces the paper's
+// grid-wide barrier per step with neighbour synchronisation that never stalls
+// unrelated warps.  Strips are loaded with 2D TMA tensor copies and written
+// back with per-row TMA tensor stores (the store tensor map ends at the last
+// interior row/column, so the ring and padding are never written).
+//
+// Three schedules drive the same strip code:
+//   RESIDENT  all strips of the grid on chip at once, every step exchanged
+//             (the grid must fit in the GPU's shared memory);
+//   BANDS     the paper's serial GPU-wide tiles: full-width bands of rows
+//             with a k-row overlapped halo above and below, k steps per visit;
+//   TILES     independent CTA tiles with a k-deep overlapped halo on all sides
+//             (no cross-CTA exchange at all), k steps per visit; also carries
+//             batches of grids.
+// Every wait is bounded by a %globaltimer deadline; on expiry the kernel
+// records J2D_ERR_TIMEOUT, stops waiting and runs to completion.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "dtb.h"
+
+namespace j2d {
+
+constexpr int kWarps = 16;            // warps (strips) per CTA
+constexpr int kThreads = kWarps * 32;
+enum { SIDE_YM = 0, SIDE_YP = 1, SIDE_XM = 2, SIDE_XP = 3 };
+enum { LINK_CONST = -1, LINK_ZERO = -2 };
+enum { MODE_BANDS = 0, MODE_TILES = 1 };
+
+// Per-grid data the kernel reads from global memory.
+struct GridDev {
+  int nx, ny, off, pad;
+  long pitch;
+  double w[5];
+  void *buf[3];  // 0 = in, 1 = workspace, 2 = out
+};
+
+struct KParams {
+  const GridDev *grids;
+  const CUtensorMap *maps;  // per grid: load maps of buf[0..2], store maps of buf[0..2]
+  const int *jobs;          // BANDS: 5 ints per wave; TILES: 7 ints per tile
+  int njobs;                // waves (BANDS) or tiles (TILES) per round
+  int rounds, depth, last_depth, src0;
+  int rmax, rp;             // strip rows (max), mailbox column length
+  int m;                    // BANDS: strips per column (per-wave value in the job)
+  int tile_wx, tile_rows;   // TILES
+  int *status;
+  int *barrier;             // grid barrier counter
+  int *gflags;              // per slot step counters (cross-CTA consumers)
+  void *gslots;             // per slot mailboxes (cross-CTA consumers)
+  unsigned long long timeout_ns;
+};
+
+// Layout of one warp's shared-memory region (elements of T).
+template <typename T>
+struct WarpLayout {
+  static constexpr int V = VecOf<T>::V;
+  static constexpr int SW = 32 * V;
+  __host__ __device__ static int mailbox_elems(int rp) { return 4 * SW + 4 * rp; }
+  __host__ __device__ static int region_elems(int rmax, int rp) {
+    const int e = rmax * SW + mailbox_elems(rp);
+    const int per128 = 128 / (int)sizeof(T);
+    return (e + per128 - 1) / per128 * per128;
+  }
+  // offsets of the mailboxes inside a mailbox block: ym[2][SW], yp[2][SW], xm[2][rp], xp[2][rp]
+  __host__ __device__ static int side_off(int side, int rp) {
+    return side == SIDE_YM ? 0 : side == SIDE_YP ? 2 * SW : side == SIDE_XM ? 4 * SW : 4 * SW + 2 * rp;
+  }
+  __host__ __device__ static int side_len(int side, int rp) { return side <= SIDE_YP ? SW : rp; }
+};
+
+constexpr int kHeaderBytes = 1024;  // mbarriers and step counters at the start of shared memory
+
+__host__ __device__ inline size_t dtb_smem_bytes(int elem, int rmax, int rp) {
+  const int SW = 32 * (16 / elem);
+  int e = rmax * SW + 4 * SW + 4 * rp;
+  const int per128 = 128 / elem;
+  e = (e + per128 - 1) / per128 * per128;
+  return (size_t)kHeaderBytes + (size_t)kWarps * e * elem;
+}
+
+// ---- bounded waits ---------------------------------------------------------
+
+__device__ __forceinline__ bool expired(uint64_t deadline, int *status) {
+  if (has_error(status)) return true;
+  if (globaltimer_ns() > deadline) {
+    set_error(status, DEV_TIMEOUT);
+    return true;
+  }
+  return false;
+}
+
+// All lanes wait until *flag >= target (acquire); false on timeout / error.
+__device__ __forceinline__ bool wait_flag(const int *flag, bool global, int target, const KParams &kp) {
+  const uint64_t deadline = globaltimer_ns() + kp.timeout_ns;
+  for (int it = 0;; ++it) {
+    const int v = global ? ld_acquire_gpu(flag) : ld_acquire_cta(flag);
+    if (__all_sync(0xffffffffu, v >= target)) return true;
+    if ((it & 63) == 63) {
+      if (__any_sync(0xffffffffu, expired(deadline, kp.status))) return false;
+      if (global) __nanosleep(64);
+    }
+  }
+}
+
+__device__ __forceinline__ bool wait_mbar(uint64_t *bar, uint32_t parity, const KParams &kp) {
+  const uint64_t deadline = globaltimer_ns() + kp.timeout_ns;
+  for (int it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 15) == 15 && expired(deadline, kp.status)) return false;
+  }
+}
+
+__device__ void grid_barrier(const KParams &kp, int &epoch) {
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    fence_acq_rel_gpu();
+    atomicAdd(kp.barrier, 1);
+    const int target = epoch * (int)gridDim.x;
+    const uint64_t deadline = globaltimer_ns() + kp.timeout_ns;
+    while (ld_acquire_gpu(kp.barrier) < target) {
+      if (expired(deadline, kp.status)) break;
+      __nanosleep(128);
+    }
+  }
+  __syncthreads();
+}
+
+// ---- strips ----------------------------------------------------------------
+
+struct Strip {
+  int g;              // grid index
+  int x0, y0, rows;   // logical coordinates of the first cell; number of rows
+  int link[4];        // neighbour slot (>= 0), LINK_CONST or LINK_ZERO
+  int ring;           // bit per side: that side is the domain ring
+  int sy0, sy1;       // rows to store (strip-relative)
+  int sx0, sx1;       // columns to store (strip-relative)
+  bool active;
+};
+
+template <typename T>
+__device__ __forceinline__ void vload(const T *p, bool global, T *o) {
+  if constexpr (sizeof(T) == 8) {
+    double2 v = global ? __ldcg(reinterpret_cast<const double2 *>(p)) : *reinterpret_cast<const double2 *>(p);
+    o[0] = v.x; o[1] = v.y;
+  } else {
+    float4 v = global ? __ldcg(reinterpret_cast<const float4 *>(p)) : *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T *p, const T *o) {
+  if constexpr (sizeof(T) == 8) {
+    *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+  } else {
+    *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+// Advance one strip by k steps: load, exchange, sweep, store.
+template <typename T, bool ADJ>
+__device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int warp, int slot, int src, int dst,
+                          int k, int base, uint32_t &mbar_phase) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  using L = WarpLayout<T>;
+  const int lane = threadIdx.x & 31;
+  const int rp = kp.rp;
+  const int region = L::region_elems(kp.rmax, rp);
+  T *wbase = reinterpret_cast<T *>(smem + kHeaderBytes);
+  T *data = wbase + (size_t)warp * region;
+  T *mbox = data + (size_t)kp.rmax * SW;  // my shared-memory mailboxes
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  int *sflags = reinterpret_cast<int *>(smem + 512);
+  const GridDev &gd = kp.grids[st.g];
+  const int nx = gd.nx, ny = gd.ny, rows = st.rows;
+  const long pitch = gd.pitch;
+  const int off = gd.off;
+  const T *srcbuf = reinterpret_cast<const T *>(gd.buf[src]);
+  T *dstbuf = reinterpret_cast<T *>(gd.buf[dst]);
+  const CUtensorMap *map_load = kp.maps + (size_t)st.g * 6 + src;
+  const CUtensorMap *map_store = kp.maps + (size_t)st.g * 6 + 3 + dst;
+  const int NW = kWarps;
+  const size_t slot_elems = (size_t)L::mailbox_elems(rp);
+  T *gslots = reinterpret_cast<T *>(kp.gslots);
+
+  // base weights W, E, S, C, N and the links of interior cells
+  const T W = (T)gd.w[0], E = (T)gd.w[1], S = (T)gd.w[2], C = (T)gd.w[3], N = (T)gd.w[4];
+  const Links<T> a = ADJ ? Links<T>{E, W, N, C, S} : Links<T>{W, E, S, C, N};
+
+  // where my incoming halos live (per side) and where my outgoing edges go
+  bool in_global[4], out_global[4], any_remote = false;
+  const T *inbox[4];
+  T *outbox[4];
+  const int *nflag[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int n = st.link[s];
+    const bool remote = n >= 0 && (n / NW) != (slot / NW);
+    in_global[s] = remote;
+    out_global[s] = remote;
+    any_remote |= remote;
+    inbox[s] = remote ? gslots + (size_t)slot * slot_elems + L::side_off(s, rp) : mbox + L::side_off(s, rp);
+    const int opp = s ^ 1;
+    if (n >= 0) {
+      outbox[s] = remote ? gslots + (size_t)n * slot_elems + L::side_off(opp, rp)
+                         : wbase + (size_t)(n % NW) * region + (size_t)kp.rmax * SW + L::side_off(opp, rp);
+      nflag[s] = remote ? kp.gflags + n : sflags + (n % NW);
+    } else {
+      outbox[s] = nullptr;
+      nflag[s] = nullptr;
+    }
+  }
+
+  // ---- load the strip (TMA) ----
+  fence_proxy_async_all();  // earlier generic writes (this warp's and, via the barriers, other CTAs') before async reads
+  __syncwarp();
+  if (lane == 0) {
+    bulk_wait_read_all();  // previous strip's stores have read shared memory
+    mbar_expect_tx(&bars[warp], (uint32_t)(SW * kp.rmax * sizeof(T)));
+    tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
+  }
+  // constant halos (ring in the forward map, overlapped-halo edge rows/columns)
+  const int xl = st.x0 + lane * V;  // logical x of this lane's element 0
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (st.link[s] >= 0) continue;
+    // the adjoint never reads ring cells (their links to the interior are removed)
+    const bool zero = st.link[s] == LINK_ZERO || (ADJ && ((st.ring >> s) & 1));
+    T *box = mbox + L::side_off(s, rp);
+    const int len = L::side_len(s, rp);
+    if (s <= SIDE_YP) {
+      const int y = s == SIDE_YM ? st.y0 - 1 : st.y0 + rows;
+      T v[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const int x = xl + e;
+        v[e] = (!zero && x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+      }
+      vstore(box + lane * V, v);
+      vstore(box + len + lane * V, v);
+    } else {
+      const int x = s == SIDE_XM ? st.x0 - 1 : st.x0 + SW;
+      for (int r = lane; r < rows; r += 32) {
+        const int y = st.y0 + r;
+        const T v = (!zero && x >= 0 && x <= nx + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+        box[r] = v;
+        box[len + r] = v;
+      }
+    }
+  }
+  // adjoint ring accumulators start from the ring values of the source
+  T acc_ym[V], acc_yp[V], acc_xm0 = 0, acc_xm1 = 0, acc_xp0 = 0, acc_xp1 = 0;
+#pragma unroll
+  for (int e = 0; e < V; ++e) { acc_ym[e] = T(0); acc_yp[e] = T(0); }
+  if (ADJ) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int x = xl + e;
+      const bool xin = x >= 1 && x <= nx;
+      if ((st.ring & (1 << SIDE_YM)) && xin) acc_ym[e] = srcbuf[off + x];
+      if ((st.ring & (1 << SIDE_YP)) && xin) acc_yp[e] = srcbuf[(long)(ny + 1) * pitch + off + x];
+    }
+    if (st.ring & (1 << SIDE_XM)) {
+      if (lane < rows) acc_xm0 = srcbuf[(long)(st.y0 + lane) * pitch + off];
+      if (lane + 32 < rows) acc_xm1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off];
+    }
+    if (st.ring & (1 << SIDE_XP)) {
+      if (lane < rows) acc_xp0 = srcbuf[(long)(st.y0 + lane) * pitch + off + nx + 1];
+      if (lane + 32 < rows) acc_xp1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1];
+    }
+  }
+  // columns beyond nx are dead: they keep their value (the ring column nx+1
+  // is read by column nx: the ring value forward, zero in the adjoint)
+  uint32_t dead = 0;
+#pragma unroll
+  for (int e = 0; e < V; ++e)
+    if (xl + e > nx) dead |= 1u << e;
+  // the element holding column nx, for the adjoint right-ring accumulation
+  const int xp_lane = (nx - st.x0) / V, xp_elem = (nx - st.x0) % V;
+
+  wait_mbar(&bars[warp], mbar_phase, kp);
+  mbar_phase ^= 1u;
+  if (ADJ && dead) {
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      if (xl + e == nx + 1)
+        for (int r = 0; r < rows; ++r) data[r * SW + lane * V + e] = T(0);
+  }
+  __syncwarp();
+
+  // ---- publish state-0 edges ----
+  auto publish_edges = [&](int par, int r, const T *o) {
+    if (r == 0 && outbox[SIDE_YM]) vstore(outbox[SIDE_YM] + par * SW + lane * V, o);
+    if (r == rows - 1 && outbox[SIDE_YP]) vstore(outbox[SIDE_YP] + par * SW + lane * V, o);
+    if (lane == 0 && outbox[SIDE_XM]) outbox[SIDE_XM][par * rp + r] = o[0];
+    if (lane == 31 && outbox[SIDE_XP]) outbox[SIDE_XP][par * rp + r] = o[V - 1];
+  };
+  auto publish_flag = [&](int value) {
+    if (any_remote) fence_acq_rel_gpu(); else fence_acq_rel_cta();
+    __syncwarp();
+    if (lane == 0) {
+      st_relaxed_cta(sflags + warp, value);
+      if (any_remote) st_relaxed_gpu(kp.gflags + slot, value);
+    }
+    __syncwarp();
+  };
+  for (int r = 0; r < rows; ++r) {
+    if (r != 0 && r != rows - 1 && !outbox[SIDE_XM] && !outbox[SIDE_XP]) continue;
+    T o[V];
+    vload(data + r * SW + lane * V, false, o);
+    publish_edges(0, r, o);
+  }
+  publish_flag(base);
+
+  // ---- k steps ----
+  for (int t = 0; t < k; ++t) {
+    const int par = t & 1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (nflag[s]) wait_flag(nflag[s], in_global[s], base + t, kp);
+    // halos of state t
+    T hym[V], hyp[V];
+    vload(inbox[SIDE_YM] + par * L::side_len(SIDE_YM, rp) + lane * V, in_global[SIDE_YM], hym);
+    vload(inbox[SIDE_YP] + par * L::side_len(SIDE_YP, rp) + lane * V, in_global[SIDE_YP], hyp);
+    T hxm0 = 0, hxm1 = 0, hxp0 = 0, hxp1 = 0;
+    {
+      const T *bx = inbox[SIDE_XM] + par * rp;
+      const T *bp = inbox[SIDE_XP] + par * rp;
+      if (lane < rows) {
+        hxm0 = in_global[SIDE_XM] ? ld_cg(bx + lane) : bx[lane];
+        hxp0 = in_global[SIDE_XP] ? ld_cg(bp + lane) : bp[lane];
+      }
+      if (lane + 32 < rows) {
+        hxm1 = in_global[SIDE_XM] ? ld_cg(bx + lane + 32) : bx[lane + 32];
+        hxp1 = in_global[SIDE_XP] ? ld_cg(bp + lane + 32) : bp[lane + 32];
+      }
+    }
+    // sweep rows top to bottom with a three-row window, updating in place
+    T prv[V], cur[V], nxt[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) prv[e] = hym[e];
+    vload(data + lane * V, false, cur);
+    for (int r = 0; r < rows; ++r) {
+      if (r + 1 < rows) {
+        vload(data + (r + 1) * SW + lane * V, false, nxt);
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) nxt[e] = hyp[e];
+      }
+      T left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+      T right = __shfl_down_sync(0xffffffffu, cur[0], 1);
+      const T hl = __shfl_sync(0xffffffffu, r < 32 ? hxm0 : hxm1, r & 31);
+      const T hr = __shfl_sync(0xffffffffu, r < 32 ? hxp0 : hxp1, r & 31);
+      if (lane == 0) left = hl;
+      if (lane == 31) right = hr;
+      T o[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const T xm = e == 0 ? left : cur[e - 1];
+        const T xp = e == V - 1 ? right : cur[e + 1];
+        o[e] = stencil(a, xm, xp, prv[e], cur[e], nxt[e]);
+      }
+      if (dead) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+          if (dead & (1u << e)) o[e] = cur[e];
+      }
+      if (ADJ && st.ring) {
+        // ring cells add their link weight times the old adjacent interior value,
+        // rounded as the one-step kernel's link chain does: the y+1 link of the
+        // bottom ring row is its last term (one fused multiply-add), the other
+        // ring sides round the product before adding it
+        if ((st.ring & (1 << SIDE_YM)) && r == 0) {
+#pragma unroll
+          for (int e = 0; e < V; ++e) acc_ym[e] = fma_rn(S, cur[e], acc_ym[e]);
+        }
+        if ((st.ring & (1 << SIDE_YP)) && r == rows - 1) {
+#pragma unroll
+          for (int e = 0; e < V; ++e) acc_yp[e] = add_rn(acc_yp[e], mul_rn(N, cur[e]));
+        }
+        if (st.ring & (1 << SIDE_XM)) {
+          const T c0 = __shfl_sync(0xffffffffu, cur[0], 0);
+          if (lane == (r & 31)) {
+            if (r < 32) acc_xm0 = add_rn(acc_xm0, mul_rn(W, c0));
+            else acc_xm1 = add_rn(acc_xm1, mul_rn(W, c0));
+          }
+        }
+        if (st.ring & (1 << SIDE_XP)) {
+          T ce = cur[0];
+#pragma unroll
+          for (int e = 1; e < V; ++e)
+            if (xp_elem == e) ce = cur[e];
+          const T cx = __shfl_sync(0xffffffffu, ce, xp_lane & 31);
+          if (lane == (r & 31)) {
+            if (r < 32) acc_xp0 = add_rn(acc_xp0, mul_rn(E, cx));
+            else acc_xp1 = add_rn(acc_xp1, mul_rn(E, cx));
+          }
+        }
+      }
+      vstore(data + r * SW + lane * V, o);
+      publish_edges(par ^ 1, r, o);
+#pragma unroll
+      for (int e = 0; e < V; ++e) { prv[e] = cur[e]; cur[e] = nxt[e]; }
+    }
+    publish_flag(base + t + 1);
+  }
+
+  // ---- store the valid part ----
+  const bool full = st.sx0 == 0 && st.sx1 == SW;
+  if (full) {
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      for (int r = st.sy0; r < st.sy1; ++r) tma_store_2d(map_store, off + st.x0, st.y0 + r, data + r * SW);
+      bulk_commit();
+      // a tensor store may rewrite the rest of the 16-byte granule holding
+      // column nx, i.e. the ring cell nx+1: let it land before the adjoint
+      // writes the ring below
+      if (ADJ && (st.ring & (1 << SIDE_XP))) {
+        bulk_wait_all();
+        fence_proxy_async_all();
+      }
+    }
+    __syncwarp();
+  } else {
+    for (int r = st.sy0; r < st.sy1; ++r) {
+      const long rowoff = (long)(st.y0 + r) * pitch + off;
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const int c = lane * V + e;
+        if (c >= st.sx0 && c < st.sx1) dstbuf[rowoff + st.x0 + c] = data[r * SW + c];
+      }
+    }
+  }
+  if (ADJ && st.ring) {
+    // ring cells of the valid region
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int c = lane * V + e, x = st.x0 + c;
+      const bool xin = x >= 1 && x <= nx && c >= st.sx0 && c < st.sx1;
+      if ((st.ring & (1 << SIDE_YM)) && xin && st.sy0 == 0) dstbuf[off + x] = acc_ym[e];
+      if ((st.ring & (1 << SIDE_YP)) && xin && st.sy1 == rows) dstbuf[(long)(ny + 1) * pitch + off + x] = acc_yp[e];
+    }
+    if ((st.ring & (1 << SIDE_XM)) && st.sx0 == 0) {
+      if (lane < rows && lane >= st.sy0 && lane < st.sy1) dstbuf[(long)(st.y0 + lane) * pitch + off] = acc_xm0;
+      if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
+        dstbuf[(long)(st.y0 + lane + 32) * pitch + off] = acc_xm1;
+    }
+    if ((st.ring & (1 << SIDE_XP)) && (nx - st.x0) < st.sx1) {
+      if (lane < rows && lane >= st.sy0 && lane < st.sy1)
+        dstbuf[(long)(st.y0 + lane) * pitch + off + nx + 1] = acc_xp0;
+      if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
+        dstbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1] = acc_xp1;
+    }
+  }
+}
+
+// Strip of slot `slot` in a band wave: columns strip j, row strip i of m.
+__device__ Strip band_strip(const KParams &kp, const int *wave, int slot, int SWc) {
+  Strip st{};
+  const GridDev &gd = kp.grids[0];
+  const int nx = gd.nx, ny = gd.ny;
+  const int by0 = wave[0], by1 = wave[1], vy0 = wave[2], vy1 = wave[3], m = wave[4];
+  const int ncs = (nx + SWc - 1) / SWc;
+  st.active = slot < ncs * m;
+  if (!st.active) return st;
+  const int j = slot / m, i = slot % m;
+  const int hb = by1 - by0, bsz = hb / m, extra = hb % m;
+  st.g = 0;
+  st.rows = bsz + (i < extra ? 1 : 0);
+  st.y0 = by0 + i * bsz + min(i, extra);
+  st.x0 = 1 + j * SWc;
+  st.active = st.rows > 0;
+  const int ylast = st.y0 + st.rows - 1;
+  st.ring = 0;
+  if (st.y0 == 1) st.ring |= 1 << SIDE_YM;
+  if (ylast == ny) st.ring |= 1 << SIDE_YP;
+  if (st.x0 == 1) st.ring |= 1 << SIDE_XM;
+  if (st.x0 <= nx && nx <= st.x0 + SWc - 1) st.ring |= 1 << SIDE_XP;
+  st.link[SIDE_YM] = i > 0 ? slot - 1 : LINK_CONST;
+  st.link[SIDE_YP] = i < m - 1 ? slot + 1 : LINK_CONST;
+  st.link[SIDE_XM] = j > 0 ? slot - m : LINK_CONST;
+  st.link[SIDE_XP] = j < ncs - 1 ? slot + m : LINK_CONST;
+  st.sy0 = max(vy0 - st.y0, 0);
+  st.sy1 = min(vy1 - st.y0, st.rows);
+  if (st.sy1 < st.sy0) st.sy1 = st.sy0;
+  st.sx0 = 0;
+  st.sx1 = SWc;
+  return st;
+}
+
+// Strip of warp w of a tile: wx across, wy down; rows per strip kp.tile_rows.
+__device__ Strip tile_strip(const KParams &kp, const int *tile, int w, int cta_slot0, int SWc) {
+  Strip st{};
+  const int g = tile[0], tx0 = tile[1], ty0 = tile[2], vx0 = tile[3], vx1 = tile[4], vy0 = tile[5], vy1 = tile[6];
+  const GridDev &gd = kp.grids[g];
+  const int nx = gd.nx, ny = gd.ny;
+  const int WX = kp.tile_wx, WY = kWarps / WX;
+  const int wx = w % WX, wy = w / WX;
+  st.g = g;
+  st.x0 = tx0 + wx * SWc;
+  st.y0 = ty0 + wy * kp.tile_rows;
+  st.active = st.x0 <= nx && st.y0 <= ny;
+  if (!st.active) return st;
+  st.rows = min(kp.tile_rows, ny + 1 - st.y0);
+  const int ylast = st.y0 + st.rows - 1;
+  st.ring = 0;
+  if (st.y0 == 1) st.ring |= 1 << SIDE_YM;
+  if (ylast == ny) st.ring |= 1 << SIDE_YP;
+  if (st.x0 == 1) st.ring |= 1 << SIDE_XM;
+  if (st.x0 <= nx && nx <= st.x0 + SWc - 1) st.ring |= 1 << SIDE_XP;
+  const bool up_ok = wy > 0;
+  const bool dn_ok = wy < WY - 1 && ylast < ny;
+  const bool lf_ok = wx > 0;
+  const bool rt_ok = wx < WX - 1 && st.x0 + SWc <= nx;
+  st.link[SIDE_YM] = up_ok ? cta_slot0 + w - WX : LINK_CONST;
+  st.link[SIDE_YP] = dn_ok ? cta_slot0 + w + WX : LINK_CONST;
+  st.link[SIDE_XM] = lf_ok ? cta_slot0 + w - 1 : LINK_CONST;
+  st.link[SIDE_XP] = rt_ok ? cta_slot0 + w + 1 : LINK_CONST;
+  st.sy0 = max(vy0 - st.y0, 0);
+  st.sy1 = min(vy1 - st.y0, st.rows);
+  if (st.sy1 < st.sy0) st.sy1 = st.sy0;
+  st.sx0 = max(vx0 - st.x0, 0);
+  st.sx1 = min(min(vx1, nx + 1) - st.x0, SWc);
+  if (st.sx1 < st.sx0) st.sx1 = st.sx0;
+  // a strip whose valid columns reach its end (or the last interior column)
+  // is stored whole with TMA; the store map clips beyond column nx
+  if (st.sx0 == 0 && st.x0 + st.sx1 >= min(vx1, nx + 1) && (vx1 > nx || st.sx1 == SWc)) st.sx1 = SWc;
+  return st;
+}
+
+template <typename T, bool ADJ, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant__ KParams kp) {
+  constexpr int SWc = 32 * VecOf<T>::V;
+  extern __shared__ __align__(1024) char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  int *sflags = reinterpret_cast<int *>(smem + 512);
+  if (lane == 0) {
+    mbar_init(&bars[warp], 1);
+    sflags[warp] = -1;
+  }
+  fence_mbar_init();
+  fence_proxy_async_smem();
+  __syncthreads();
+  uint32_t phase = 0;
+  int epoch = 0;
+  const int slot = blockIdx.x * kWarps + warp;
+  const int kmax1 = max(kp.depth, kp.last_depth) + 1;
+  int seq = 0;  // strips processed by this CTA (tiles) / waves (bands)
+  for (int r = 0; r < kp.rounds; ++r) {
+    const int dst = ((kp.rounds - 1 - r) & 1) == 0 ? 2 : 1;
+    const int src = r == 0 ? kp.src0 : (((kp.rounds - r) & 1) == 0 ? 2 : 1);
+    const int k = r == kp.rounds - 1 ? kp.last_depth : kp.depth;
+    if (MODE == MODE_BANDS) {
+      for (int wv = 0; wv < kp.njobs; ++wv, ++seq) {
+        const Strip st = band_strip(kp, kp.jobs + 5 * wv, slot, SWc);
+        if (st.active) run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        if (lane == 0) {
+          bulk_wait_all();
+          fence_proxy_async_global();
+        }
+        grid_barrier(kp, epoch);
+      }
+    } else {
+      for (int j = blockIdx.x; j < kp.njobs; j += gridDim.x, ++seq) {
+        const Strip st = tile_strip(kp, kp.jobs + 7 * j, warp, blockIdx.x * kWarps, SWc);
+        if (st.active) run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        __syncthreads();
+      }
+      if (lane == 0) {
+        bulk_wait_all();
+        fence_proxy_async_global();
+      }
+      grid_barrier(kp, epoch);
+    }
+  }
+  if (lane == 0) bulk_wait_all();
+}
+
+// ---- host side -------------------------------------------------------------
+
+int dtb_rows_max(j2d_dtype dt, size_t smem_optin, int warps) {
+  const int elem = dt == J2D_F64 ? 8 : 4;
+  (void)warps;
+  for (int r = 64; r >= 1; --r) {
+    const int rp = (r + 3) / 4 * 4;
+    if (dtb_smem_bytes(elem, r, rp) <= smem_optin) return r;
+  }
+  return 0;
+}
+
+static int vec_of(j2d_dtype dt) { return dt == J2D_F64 ? 2 : 4; }
+
+// Resident fit: strips per column m and rows per strip for one grid on `ctas` CTAs.
+static bool resident_fit(const GridDesc &g, int sw, int ctas, int rmax, int *m_out) {
+  const int ncs = (g.nx + sw - 1) / sw;
+  const long slots = (long)ctas * kWarps;
+  if (ncs > slots) return false;
+  int m = (int)std::min<long>(slots / ncs, g.ny);
+  if ((g.ny + m - 1) / m > rmax) return false;
+  *m_out = m;
+  return true;
+}
+
+DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, size_t smem_optin,
+                     const DtbRequest &rq) {
+  DtbConfig c;
+  c.ctas = rq.ctas > 0 ? std::min(rq.ctas, sms) : sms;
+  c.rows = dtb_rows_max(dt, smem_optin, kWarps);
+  const int sw = 32 * vec_of(dt);
+  int algo = rq.algo;
+  const bool single = grids.size() == 1;
+  int m = 0;
+  const bool fits = single && resident_fit(grids[0], sw, c.ctas, c.rows, &m);
+  if (algo == J2D_ALGO_AUTO) {
+    if (rq.steps < 4) algo = J2D_ALGO_ONESTEP;
+    else if (fits) algo = J2D_ALGO_RESIDENT;
+    else if (dt == J2D_F32 || !single) algo = J2D_ALGO_TILES;
+    else algo = J2D_ALGO_ONESTEP;
+  }
+  if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
+  if (algo == J2D_ALGO_BANDS && !single) algo = J2D_ALGO_TILES;
+  c.algo = algo;
+  c.depth = rq.depth > 0 ? rq.depth : (dt == J2D_F64 ? 4 : 8);
+  c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : 2;
+  if (algo == J2D_ALGO_RESIDENT) c.depth = (int)std::max<long>(rq.steps, 1);
+  return c;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+static bool encode_map(CUtensorMap *m, j2d_dtype dt, void *base, long pitch, long width, long height, int boxw,
+                       int boxh) {
+  auto enc = get_encoder();
+  if (!enc) return false;
+  const size_t elem = dt == J2D_F64 ? 8 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * elem)};
+  cuuint32_t box[2] = {(cuuint32_t)boxw, (cuuint32_t)boxh};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, dt == J2D_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+                   dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Overlapped covering of [1, n] by windows of `win` cells with a `g`-cell halo:
+// returns (start, valid_begin, valid_end) triples; `align` keeps starts ≡ 1 mod align.
+static std::vector<int> cover(int n, int win, int g) {
+  std::vector<int> out;
+  int v = 1;
+  while (v <= n) {
+    const int s = v == 1 ? 1 : v - g;
+    const int e = s + win;  // exclusive
+    const int ve = e > n ? n + 1 : e - g;
+    out.push_back(s);
+    out.push_back(v);
+    out.push_back(ve);
+    if (ve <= v) break;  // halo too deep for the window
+    v = ve;
+  }
+  return out;
+}
+
+static void ensure(void *&p, size_t &cap, size_t need, cudaError_t &err) {
+  if (cap >= need) return;
+  cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  err = cudaMalloc(&p, need);
+  if (err == cudaSuccess) cap = need;
+}
+
+template <typename T>
+static void *kernel_ptr(int mode, bool adj) {
+  if (mode == MODE_BANDS) return adj ? (void *)dtb_kernel<T, true, MODE_BANDS> : (void *)dtb_kernel<T, false, MODE_BANDS>;
+  return adj ? (void *)dtb_kernel<T, true, MODE_TILES> : (void *)dtb_kernel<T, false, MODE_TILES>;
+}
+
+cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &err) {
+  const auto &grids = *r.grids;
+  const j2d_dtype dt = r.dtype;
+  const int V = vec_of(dt), SW = 32 * V;
+  const size_t elem = dt == J2D_F64 ? 8 : 4;
+  const int ctas = r.cfg.ctas;
+  const int rmax = dtb_rows_max(dt, r.smem_optin, kWarps);
+  const int rp = (rmax + 3) / 4 * 4;
+  if (rmax < 2) { err = "shared memory too small"; return cudaErrorNotSupported; }
+  const int mode = (r.cfg.algo == J2D_ALGO_TILES) ? MODE_TILES : MODE_BANDS;
+  const bool single = grids.size() == 1;
+  if (mode == MODE_BANDS && !single) { err = "bands/resident need a single grid"; return cudaErrorNotSupported; }
+
+  KParams kp{};
+  std::vector<int> jobs;
+  int depth = r.cfg.depth, rounds = 1, last = (int)r.steps;
+  if (r.cfg.algo == J2D_ALGO_RESIDENT) {
+    int m = 0;
+    if (!resident_fit(grids[0], SW, ctas, rmax, &m)) { err = "grid does not fit on chip"; return cudaErrorNotSupported; }
+    depth = last = (int)r.steps;
+    rounds = 1;
+    jobs = {1, grids[0].ny + 1, 1, grids[0].ny + 1, m};
+  } else {
+    depth = std::max(1, std::min(depth, (int)r.steps));
+    rounds = (int)((r.steps + depth - 1) / depth);
+    last = (int)(r.steps - (long)(rounds - 1) * depth);
+    if (mode == MODE_BANDS) {
+      const GridDesc &g = grids[0];
+      const int ncs = (g.nx + SW - 1) / SW;
+      const long slots = (long)ctas * kWarps;
+      if (ncs > slots) { err = "grid too wide for one band"; return cudaErrorNotSupported; }
+      const int m = (int)std::min<long>(slots / ncs, g.ny);
+      const int hb = m * rmax;
+      if (hb <= 2 * depth) { err = "band too short for the temporal depth"; return cudaErrorNotSupported; }
+      auto cv = cover(g.ny, hb, depth);
+      for (size_t i = 0; i + 2 < cv.size(); i += 3) {
+        const int bs = cv[i], ve = cv[i + 2];
+        const int be = std::min(g.ny + 1, bs + hb);
+        const int mm = std::min(m, be - bs);
+        jobs.insert(jobs.end(), {bs, be, cv[i + 1], ve, mm});
+      }
+    } else {
+      const int wx = r.cfg.tile_wx, wy = kWarps / wx;
+      const int trows = rmax;
+      const int tw = wx * SW, th = wy * trows;
+      const int gx = (depth + V - 1) / V * V;
+      if (tw <= 2 * gx || th <= 2 * depth) { err = "tile too small for the temporal depth"; return cudaErrorNotSupported; }
+      for (size_t gi = 0; gi < grids.size(); ++gi) {
+        const GridDesc &g = grids[gi];
+        auto cx = cover(g.nx, tw, gx), cy = cover(g.ny, th, depth);
+        for (size_t a = 0; a + 2 < cy.size(); a += 3)
+          for (size_t b = 0; b + 2 < cx.size(); b += 3)
+            jobs.insert(jobs.end(), {(int)gi, cx[b], cy[a], cx[b + 1], cx[b + 2], cy[a + 1], cy[a + 2]});
+      }
+      kp.tile_wx = wx;
+      kp.tile_rows = trows;
+    }
+  }
+  const int njobs = (int)(jobs.size() / (mode == MODE_BANDS ? 5 : 7));
+
+  // descriptors: grids, tensor maps, jobs
+  const size_t ng = grids.size();
+  const size_t off_maps = (ng * sizeof(GridDev) + 127) / 128 * 128;
+  const size_t off_jobs = off_maps + ng * 6 * sizeof(CUtensorMap);
+  const size_t desc_bytes = off_jobs + jobs.size() * sizeof(int) + 16;
+  std::vector<char> host(desc_bytes, 0);
+  GridDev *hg = reinterpret_cast<GridDev *>(host.data());
+  CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(host.data() + off_maps);
+  bool in_is_out = false;
+  for (size_t i = 0; i < ng; ++i) {
+    const GridDesc &g = grids[i];
+    hg[i].nx = g.nx;
+    hg[i].ny = g.ny;
+    hg[i].off = (int)g.off;
+    hg[i].pitch = g.pitch;
+    for (int d = 0; d < 5; ++d) hg[i].w[d] = g.w[d];
+    hg[i].buf[0] = const_cast<void *>(r.in[i]);
+    hg[i].buf[1] = r.ws[i];
+    hg[i].buf[2] = r.out[i];
+    if (r.in[i] == r.out[i]) in_is_out = true;
+    for (int b = 0; b < 3; ++b) {
+      if (!encode_map(&hm[i * 6 + b], dt, hg[i].buf[b], g.pitch, g.off + g.nx + 2, g.ny + 2, SW, rmax) ||
+          !encode_map(&hm[i * 6 + 3 + b], dt, hg[i].buf[b], g.pitch, g.off + g.nx + 1, g.ny + 1, SW, 1)) {
+        err = "cuTensorMapEncodeTiled failed";
+        return cudaErrorNotSupported;
+      }
+    }
+  }
+  memcpy(host.data() + off_jobs, jobs.data(), jobs.size() * sizeof(int));
+  cudaError_t e = cudaSuccess;
+  ensure(S.desc, S.desc_bytes, desc_bytes, e);
+  if (e != cudaSuccess) { err = "descriptor allocation"; return cudaErrorMemoryAllocation; }
+  const size_t slot_bytes = (size_t)WarpLayout<double>::mailbox_elems(rp) * 8;  // sized for the larger type
+  const size_t nslots = (size_t)ctas * kWarps;
+  const size_t scratch = 256 + nslots * sizeof(int) + (mode == MODE_BANDS ? nslots * slot_bytes : 0);
+  ensure(S.scratch, S.scratch_bytes, scratch, e);
+  if (e != cudaSuccess) { err = "scratch allocation"; return cudaErrorMemoryAllocation; }
+  if ((e = cudaMemcpyAsync(S.desc, host.data(), desc_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+    err = "descriptor upload";
+    return e;
+  }
+  char *sc = (char *)S.scratch;
+  if ((e = cudaMemsetAsync(sc, 0, 256, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(sc + 256, 0xff, nslots * sizeof(int), s)) != cudaSuccess) {
+    err = "scratch reset";
+    return e;
+  }
+
+  // ring of every buffer a round writes = ring of the input (constant forward;
+  // corners and the starting values of the adjoint ring accumulation)
+  int src0 = 0;
+  for (size_t i = 0; i < ng; ++i) {
+    if (r.out[i] != r.in[i] && (e = launch_ring_copy(dt, r.in[i], r.out[i], grids[i], s)) != cudaSuccess) return e;
+    if (rounds > 1 && (e = launch_ring_copy(dt, r.in[i], r.ws[i], grids[i], s)) != cudaSuccess) return e;
+  }
+  // overlapped halos read neighbours' cells: a round must not write its source
+  const int dst0 = ((rounds - 1) & 1) == 0 ? 2 : 1;
+  if (in_is_out && dst0 == 2 && r.cfg.algo != J2D_ALGO_RESIDENT) {
+    for (size_t i = 0; i < ng; ++i)
+      if ((e = cudaMemcpyAsync(r.ws[i], r.in[i], grids[i].bytes(elem), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+    src0 = 1;
+  }
+
+  kp.grids = reinterpret_cast<const GridDev *>(S.desc);
+  kp.maps = reinterpret_cast<const CUtensorMap *>((char *)S.desc + off_maps);
+  kp.jobs = reinterpret_cast<const int *>((char *)S.desc + off_jobs);
+  kp.njobs = njobs;
+  kp.rounds = rounds;
+  kp.depth = depth;
+  kp.last_depth = last;
+  kp.src0 = src0;
+  kp.rmax = rmax;
+  kp.rp = rp;
+  kp.status = r.status;
+  kp.barrier = reinterpret_cast<int *>(sc);
+  kp.gflags = reinterpret_cast<int *>(sc + 256);
+  kp.gslots = sc + 256 + nslots * sizeof(int);
+  kp.timeout_ns = r.timeout_ns;
+
+  const size_t smem = dtb_smem_bytes((int)elem, rmax, rp);
+  void *fn = dt == J2D_F64 ? kernel_ptr<double>(mode, r.adjoint) : kernel_ptr<float>(mode, r.adjoint);
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+    err = "shared memory attribute";
+    return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void *args[] = {&kp};
+  note_launch();
+  e = cudaLaunchKernelExC(&cfg, fn, args);
+  if (e != cudaSuccess) err = "cooperative launch";
+  return e;
+}
+
+void dtb_release(DtbState &S) {
+  cudaFree(S.scratch);
+  cudaFree(S.desc);
+  S = DtbState{};
+}
+
+}  // namespace j2d

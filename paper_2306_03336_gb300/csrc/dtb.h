@@ -1,0 +1,56 @@
+// dtb.h -- host interface of the temporally blocked kernels (dtb.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct j2d5pt_plan_s;
+
+namespace j2d {
+
+struct DtbRequest {
+  int algo = J2D_ALGO_AUTO;
+  int depth = 0;
+  int tile_wx = 0;
+  int ctas = 0;
+  long steps = 0;
+  bool adjoint = false;
+};
+
+// Everything one temporally blocked run needs.
+struct DtbRun {
+  j2d_dtype dtype = J2D_F64;
+  const std::vector<GridDesc> *grids = nullptr;
+  const void *const *in = nullptr;
+  void *const *out = nullptr;
+  void **ws = nullptr;
+  long steps = 0;
+  bool adjoint = false;
+  DtbConfig cfg;
+  int *status = nullptr;
+  unsigned long long timeout_ns = 0;
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+
+// Device scratch and cached launch data owned by a plan.
+struct DtbState {
+  void *scratch = nullptr;  // barrier counter, flags, halo mailboxes
+  size_t scratch_bytes = 0;
+  void *desc = nullptr;     // grid descriptors, tensor maps, job lists
+  size_t desc_bytes = 0;
+  void *host_desc = nullptr;  // pinned staging for `desc`
+  size_t host_desc_bytes = 0;
+};
+
+// Largest rows per warp strip that fit in shared memory.
+int dtb_rows_max(j2d_dtype dt, size_t smem_optin, int warps);
+
+DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, size_t smem_optin,
+                     const DtbRequest &rq);
+cudaError_t dtb_run(DtbState &st, const DtbRun &r, cudaStream_t s, std::string &err);
+void dtb_release(DtbState &st);
+
+}  // namespace j2d

@@ -1,0 +1,49 @@
+// internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/j2d5pt.h"
+
+namespace j2d {
+
+// One grid of a plan: interior sizes, layout and weights {W, E, S, C, N}.
+struct GridDesc {
+  int nx = 0, ny = 0;
+  long pitch = 0;  // elements per row
+  long off = 0;    // element offset of logical column 0
+  double w[5] = {0, 0, 0, 0, 0};
+  size_t bytes(size_t elem) const { return (size_t)(ny + 2) * (size_t)pitch * elem; }
+};
+
+// Geometry of the temporally blocked kernels (chosen by the planner / tuner).
+struct DtbConfig {
+  int algo = J2D_ALGO_ONESTEP;  // resolved algorithm
+  int depth = 1;                // steps per on-chip visit (BANDS / TILES)
+  int tile_wx = 4;              // TILES: strips across a tile
+  int ctas = 0;                 // persistent grid size
+  int rows = 0;                 // rows per warp strip
+};
+
+// Device scratch for the temporally blocked kernels.
+struct DtbScratch {
+  void *base = nullptr;
+  size_t bytes = 0;
+};
+
+// Count of kernels launched by the library (j2d5pt_kernel_launches).
+extern std::atomic<long> g_launches;
+inline void note_launch(long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, cudaStream_t s);
+cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const GridDesc &g, cudaStream_t s);
+long wgrad_partial_count(j2d_dtype dt, const GridDesc &g);
+cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,
+                         const GridDesc &g, cudaStream_t s);
+cudaError_t measure_fma(j2d_dtype dt, double *rate);
+
+}  // namespace j2d

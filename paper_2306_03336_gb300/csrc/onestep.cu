@@ -1,0 +1,343 @@
+// onestep.cu -- the one-step j2d5pt kernel (time loop on the host, every step
+// streams the grid through HBM), plus the ring copy, the weight-gradient
+// reduction and the FMA-rate probe.
+//
+// One-step kernel (Zhang et al., GPGPU'23, Section 3.1, Listing 1 with the
+// pointers in global memory): each thread owns one 16-byte vector of columns
+// and ROWS consecutive rows.  It loads its ROWS+2 rows into registers (the
+// listing's column cache t[ILP+2]), takes the x-1 / x+1 neighbours across the
+// vector boundary from the adjacent lane with a warp shuffle (lane 0 and lane
+// 31 read the one value beyond the warp from L1), and writes ROWS results.
+// Every cell of the logical array, ring included, is produced: ring and
+// outside cells through the identity links (forward) or the transposed ring
+// links (adjoint) of cell_links(), so one kernel serves both directions.
+#include "common.cuh"
+#include "internal.h"
+
+namespace j2d {
+
+constexpr int kWarpsX = 8;  // warps side by side in a block
+
+template <typename T, int V>
+__device__ __forceinline__ void unpack(const typename VecOf<T>::type &v, T *o);
+template <>
+__device__ __forceinline__ void unpack<double, 2>(const double2 &v, double *o) { o[0] = v.x; o[1] = v.y; }
+template <>
+__device__ __forceinline__ void unpack<float, 4>(const float4 &v, float *o) {
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ double2 pack(const double *o, double2 *) { return make_double2(o[0], o[1]); }
+__device__ __forceinline__ float4 pack(const float *o, float4 *) { return make_float4(o[0], o[1], o[2], o[3]); }
+
+template <typename T, bool ADJ, int ROWS>
+__global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, T *__restrict__ out, long pitch,
+                                                      int off, int nx, int ny, Weights<T> w) {
+  constexpr int V = VecOf<T>::V;
+  using VT = typename VecOf<T>::type;
+  const int lane = threadIdx.x;
+  const long pc0 = (((long)blockIdx.x * kWarpsX + threadIdx.y) * 32 + lane) * V;
+  const bool live = pc0 < pitch;
+  const int xl0 = (int)(pc0 - off);  // logical x of element 0
+  const int y0 = blockIdx.y * ROWS;
+  const int H = ny + 2;
+
+  T t[ROWS + 2][V];
+#pragma unroll
+  for (int r = 0; r < ROWS + 2; ++r) {
+    const int y = y0 - 1 + r;
+    if (live && y >= 0 && y < H) {
+      unpack<T, V>(*reinterpret_cast<const VT *>(in + (long)y * pitch + pc0), t[r]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) t[r][v] = T(0);
+    }
+  }
+  // Elements outside the logical array (row padding) read as zero.
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int x = xl0 + v;
+    if (x < 0 || x > nx + 1) {
+#pragma unroll
+      for (int r = 0; r < ROWS + 2; ++r) t[r][v] = T(0);
+    }
+  }
+
+  Links<T> cw[V];  // links of this thread's columns on rows away from the ring
+#pragma unroll
+  for (int v = 0; v < V; ++v) cw[v] = cell_links<T, ADJ>(xl0 + v, ADJ ? 2 : 1, nx, ny, w);
+
+  const bool lval = live && (xl0 - 1 >= 0) && (xl0 - 1 <= nx + 1);
+  const bool rval = live && (xl0 + V <= nx + 1);
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int y = y0 + r;
+    if (y >= H) break;
+    T left = __shfl_up_sync(0xffffffffu, t[r + 1][V - 1], 1);
+    T right = __shfl_down_sync(0xffffffffu, t[r + 1][0], 1);
+    if (lane == 0) left = lval ? in[(long)y * pitch + pc0 - 1] : T(0);
+    if (lane == 31) right = rval ? in[(long)y * pitch + pc0 + V] : T(0);
+    const bool mid = ADJ ? (y >= 2 && y <= ny - 1) : (y >= 1 && y <= ny);
+    T o[V];
+    if (mid) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const T xm = v == 0 ? left : t[r + 1][v - 1];
+        const T xp = v == V - 1 ? right : t[r + 1][v + 1];
+        o[v] = stencil(cw[v], xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const T xm = v == 0 ? left : t[r + 1][v - 1];
+        const T xp = v == V - 1 ? right : t[r + 1][v + 1];
+        o[v] = stencil(cell_links<T, ADJ>(xl0 + v, y, nx, ny, w), xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
+      }
+    }
+    if (live) *reinterpret_cast<VT *>(out + (long)y * pitch + pc0) = pack(o, (VT *)nullptr);
+  }
+}
+
+// Copy the ring (rows 0 and ny+1, columns 0 and nx+1) of `in` to `out`.
+template <typename T>
+__global__ void ring_copy_kernel(const T *__restrict__ in, T *__restrict__ out, long pitch, int off, int nx,
+                                 int ny) {
+  const int n_rows = 2 * (nx + 2), n = n_rows + 2 * ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int y, x;
+    if (i < n_rows) {
+      y = (i < nx + 2) ? 0 : ny + 1;
+      x = i % (nx + 2);
+    } else {
+      const int j = i - n_rows;
+      y = 1 + (j >> 1);
+      x = (j & 1) ? nx + 1 : 0;
+    }
+    const long e = (long)y * pitch + off + x;
+    out[e] = in[e];
+  }
+}
+
+// Weight-gradient partial sums: per block, sum over its cells of
+// lam[i] * u[nbr_d(i)] for d = x-1, x+1, y-1, centre, y+1, in FP64, reduced in
+// a fixed order (thread order, xor tree, warp order) so results are
+// reproducible.
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(256) wgrad_kernel(const T *__restrict__ u, const T *__restrict__ lam, long pitch,
+                                                    int off, int nx, int ny, double *__restrict__ partials) {
+  constexpr int V = VecOf<T>::V;
+  using VT = typename VecOf<T>::type;
+  const int lane = threadIdx.x;
+  const long pc0 = (((long)blockIdx.x * kWarpsX + threadIdx.y) * 32 + lane) * V;
+  const bool live = pc0 < pitch;
+  const int xl0 = (int)(pc0 - off);
+  const int y0 = 1 + blockIdx.y * ROWS;  // interior rows only
+  T t[ROWS + 2][V];
+#pragma unroll
+  for (int r = 0; r < ROWS + 2; ++r) {
+    const int y = y0 - 1 + r;
+    if (live && y <= ny + 1) {
+      unpack<T, V>(*reinterpret_cast<const VT *>(u + (long)y * pitch + pc0), t[r]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) t[r][v] = T(0);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int x = xl0 + v;
+    if (x < 0 || x > nx + 1) {
+#pragma unroll
+      for (int r = 0; r < ROWS + 2; ++r) t[r][v] = T(0);
+    }
+  }
+  const bool lval = live && (xl0 - 1 >= 0) && (xl0 - 1 <= nx + 1);
+  const bool rval = live && (xl0 + V <= nx + 1);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int y = y0 + r;
+    if (y > ny) break;
+    T left = __shfl_up_sync(0xffffffffu, t[r + 1][V - 1], 1);
+    T right = __shfl_down_sync(0xffffffffu, t[r + 1][0], 1);
+    if (lane == 0) left = lval ? u[(long)y * pitch + pc0 - 1] : T(0);
+    if (lane == 31) right = rval ? u[(long)y * pitch + pc0 + V] : T(0);
+    T g[V];
+    if (live) {
+      unpack<T, V>(*reinterpret_cast<const VT *>(lam + (long)y * pitch + pc0), g);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) g[v] = T(0);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int x = xl0 + v;
+      if (x < 1 || x > nx) continue;
+      const double gv = (double)g[v];
+      const double xm = (double)(v == 0 ? left : t[r + 1][v - 1]);
+      const double xp = (double)(v == V - 1 ? right : t[r + 1][v + 1]);
+      acc[0] = fma(gv, xm, acc[0]);
+      acc[1] = fma(gv, xp, acc[1]);
+      acc[2] = fma(gv, (double)t[r][v], acc[2]);
+      acc[3] = fma(gv, (double)t[r + 1][v], acc[3]);
+      acc[4] = fma(gv, (double)t[r + 2][v], acc[4]);
+    }
+  }
+  __shared__ double red[kWarpsX][5];
+#pragma unroll
+  for (int d = 0; d < 5; ++d) {
+    double s = acc[d];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[threadIdx.y][d] = s;
+  }
+  __syncthreads();
+  if (threadIdx.y == 0 && lane < 5) {
+    double s = 0.0;
+    for (int wi = 0; wi < kWarpsX; ++wi) s += red[wi][lane];
+    partials[((long)blockIdx.y * gridDim.x + blockIdx.x) * 5 + lane] = s;
+  }
+}
+
+// dw[d] += sum of the partials in a fixed order (one block).
+__global__ void wgrad_final_kernel(const double *__restrict__ partials, long nblocks, double *__restrict__ dw) {
+  __shared__ double red[256][5];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (long b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int d = 0; d < 5; ++d) acc[d] += partials[b * 5 + d];
+  for (int d = 0; d < 5; ++d) red[threadIdx.x][d] = acc[d];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int d = 0; d < 5; ++d) red[threadIdx.x][d] += red[threadIdx.x + s][d];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) dw[threadIdx.x] += red[0][threadIdx.x];
+}
+
+// FMA throughput probe: eight independent chains per thread.
+template <typename T>
+__global__ void fma_rate_kernel(T *out, int iters, T a, T b) {
+  T r0 = threadIdx.x, r1 = r0 + 1, r2 = r0 + 2, r3 = r0 + 3, r4 = r0 + 4, r5 = r0 + 5, r6 = r0 + 6, r7 = r0 + 7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      r0 = fma_rn(r0, a, b); r1 = fma_rn(r1, a, b); r2 = fma_rn(r2, a, b); r3 = fma_rn(r3, a, b);
+      r4 = fma_rn(r4, a, b); r5 = fma_rn(r5, a, b); r6 = fma_rn(r6, a, b); r7 = fma_rn(r7, a, b);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r0 + r1 + r2 + r3 + r4 + r5 + r6 + r7;
+}
+
+// ---- host launchers --------------------------------------------------------
+
+template <typename T>
+static Weights<T> cast_weights(const double *w) {
+  Weights<T> r;
+  for (int i = 0; i < 5; ++i) r.w[i] = (T)w[i];
+  return r;
+}
+
+constexpr int kOneRows = 8;
+
+static dim3 onestep_grid(const GridDesc &g, int vec, int rows, int row0) {
+  const long cols_per_block = (long)vec * 32 * kWarpsX;
+  return dim3((unsigned)((g.pitch + cols_per_block - 1) / cols_per_block),
+              (unsigned)((g.ny + 2 - row0 + rows - 1) / rows));
+}
+
+std::atomic<long> g_launches{0};
+
+cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, cudaStream_t s) {
+  note_launch();
+  const dim3 blk(32, kWarpsX);
+  if (dt == J2D_F64) {
+    const dim3 grd = onestep_grid(g, 2, kOneRows, 0);
+    auto w = cast_weights<double>(g.w);
+    if (adj)
+      onestep_kernel<double, true, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
+                                                                 (int)g.off, g.nx, g.ny, w);
+    else
+      onestep_kernel<double, false, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
+                                                                  (int)g.off, g.nx, g.ny, w);
+  } else {
+    const dim3 grd = onestep_grid(g, 4, kOneRows, 0);
+    auto w = cast_weights<float>(g.w);
+    if (adj)
+      onestep_kernel<float, true, kOneRows><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
+                                                                (int)g.off, g.nx, g.ny, w);
+    else
+      onestep_kernel<float, false, kOneRows><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
+                                                                 (int)g.off, g.nx, g.ny, w);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const GridDesc &g, cudaStream_t s) {
+  const int n = 2 * (g.nx + 2) + 2 * g.ny;
+  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  note_launch();
+  if (dt == J2D_F64)
+    ring_copy_kernel<double><<<blocks, 256, 0, s>>>((const double *)in, (double *)out, g.pitch, (int)g.off, g.nx, g.ny);
+  else
+    ring_copy_kernel<float><<<blocks, 256, 0, s>>>((const float *)in, (float *)out, g.pitch, (int)g.off, g.nx, g.ny);
+  return cudaGetLastError();
+}
+
+long wgrad_partial_count(j2d_dtype dt, const GridDesc &g) {
+  GridDesc gi = g;
+  const dim3 grd = onestep_grid(gi, dt == J2D_F64 ? 2 : 4, kOneRows, 2);
+  return (long)grd.x * grd.y;
+}
+
+cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,
+                         const GridDesc &g, cudaStream_t s) {
+  const dim3 blk(32, kWarpsX);
+  const dim3 grd = onestep_grid(g, dt == J2D_F64 ? 2 : 4, kOneRows, 2);
+  note_launch(2);
+  if (dt == J2D_F64)
+    wgrad_kernel<double, kOneRows><<<grd, blk, 0, s>>>((const double *)u, (const double *)lam, g.pitch, (int)g.off,
+                                                       g.nx, g.ny, partials);
+  else
+    wgrad_kernel<float, kOneRows><<<grd, blk, 0, s>>>((const float *)u, (const float *)lam, g.pitch, (int)g.off,
+                                                      g.nx, g.ny, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  wgrad_final_kernel<<<1, 256, 0, s>>>(partials, (long)grd.x * grd.y, dw);
+  return cudaGetLastError();
+}
+
+cudaError_t measure_fma(j2d_dtype dt, double *rate) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int blk = 256, grid = sms * 8;
+  const int iters = dt == J2D_F64 ? 400 : 8000;
+  void *buf = nullptr;
+  if ((e = cudaMalloc(&buf, sizeof(double) * grid * blk)) != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    if (dt == J2D_F64)
+      fma_rate_kernel<double><<<grid, blk>>>((double *)buf, iters, 0.999, 0.001);
+    else
+      fma_rate_kernel<float><<<grid, blk>>>((float *)buf, iters, 0.999f, 0.001f);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return e;
+  *rate = (double)grid * blk * iters * 64 / (best * 1e-3);
+  return cudaSuccess;
+}
+
+}  // namespace j2d
