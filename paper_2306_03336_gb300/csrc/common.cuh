@@ -2,8 +2,8 @@
 //
 // The stencil (Zhang et al., GPGPU'23, Section 3.1, Listing 1) updates a cell
 // from its x-1, x+1, y-1, centre and y+1 neighbours with weights W, E, S, C, N.
-// Every kernel here evaluates it as one product followed by four fused
-// multiply-adds in that operand order, so the one-step kernel and the
+// Every kernel here evaluates it with the same chain of one product and four
+// fused multiply-adds (stencil() below), so the one-step kernel and the
 // temporally blocked kernels give bit-identical results for the same inputs.
 #pragma once
 
@@ -33,14 +33,17 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-// One cell update: product of the x-1 link, then fused multiply-adds of the
-// x+1, y-1, centre and y+1 links (the operand order of Listing 1).
+// One cell update: the product of the y-1 link, then fused multiply-adds of
+// the centre, x-1, x+1 and y+1 links.  The order starts with the operands a
+// row sweep already holds in registers and ends with the ones that arrive
+// last (lane shuffles, the next row), so the chain does not wait on them.
+// Every kernel uses this one order: results are bit-identical across kernels.
 template <typename T>
 __device__ __forceinline__ T stencil(const Links<T> &a, T xm, T xp, T ym, T c, T yp) {
-  T r = mul_rn(a.xm, xm);
-  r = fma_rn(a.xp, xp, r);
-  r = fma_rn(a.ym, ym, r);
+  T r = mul_rn(a.ym, ym);
   r = fma_rn(a.c, c, r);
+  r = fma_rn(a.xm, xm, r);
+  r = fma_rn(a.xp, xp, r);
   r = fma_rn(a.yp, yp, r);
   return r;
 }
@@ -101,6 +104,35 @@ __device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory vector / scalar access on 32-bit shared addresses.  volatile:
+// kept in program order with the other shared-memory accesses of the warp
+// (the strip is updated in place).
+template <typename T> __device__ __forceinline__ void lds_v(uint32_t a, T *o);
+template <> __device__ __forceinline__ void lds_v<double>(uint32_t a, double *o) {
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(o[0]), "=d"(o[1]) : "r"(a) : "memory");
+}
+template <> __device__ __forceinline__ void lds_v<float>(uint32_t a, float *o) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]) : "r"(a) : "memory");
+}
+template <typename T> __device__ __forceinline__ void sts_v(uint32_t a, const T *o);
+template <> __device__ __forceinline__ void sts_v<double>(uint32_t a, const double *o) {
+  asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(o[0]), "d"(o[1]) : "memory");
+}
+template <> __device__ __forceinline__ void sts_v<float>(uint32_t a, const float *o) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(o[0]), "f"(o[1]), "f"(o[2]), "f"(o[3]) : "memory");
+}
+template <typename T> __device__ __forceinline__ T lds_s(uint32_t a);
+template <> __device__ __forceinline__ double lds_s<double>(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+template <> __device__ __forceinline__ float lds_s<float>(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
 }
 
 // mbarrier (shared memory transaction barrier) for TMA completion.

@@ -181,7 +181,99 @@ __device__ __forceinline__ void vstore(T *p, const T *o) {
   }
 }
 
-// Advance one strip by k steps: load, exchange, sweep, store.
+// Adjoint ring accumulators of a strip bordering the ring (unused forward).
+template <typename T>
+struct RingAcc {
+  T ym[VecOf<T>::V], yp[VecOf<T>::V];  // ring rows 0 and ny+1, this lane's columns
+  T xm0, xm1, xp0, xp1;                // ring columns 0 and nx+1, rows lane and lane+32
+  int ring, xp_lane, xp_elem;
+  T W, E, S, N;
+};
+
+// One time step over a strip held in shared memory, swept row by row with a
+// three-row register window and updated in place.  Only this warp's own
+// shared memory is touched: the halo rows come in registers, the halo column
+// from the warp's mailbox (lane 0 reads the x-1 column, lane 31 the x+1 one).
+template <typename T, bool ADJ, bool DEAD>
+__device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int lane, const Links<T> &a,
+                                           const T *hym, const T *hyp, uint32_t dead, RingAcc<T> &rg) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  T ra[V], rb[V], rc[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) ra[e] = hym[e];
+  vload(drow, false, rb);
+#pragma unroll 2
+  for (int r = 0; r < rows; ++r) {
+    if (r + 1 < rows) {
+      vload(drow + (r + 1) * SW, false, rc);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) rc[e] = hyp[e];
+    }
+    const T h = hcol[r];
+    T left = __shfl_up_sync(0xffffffffu, rb[V - 1], 1);
+    T right = __shfl_down_sync(0xffffffffu, rb[0], 1);
+    if (lane == 0) left = h;
+    if (lane == 31) right = h;
+    T o[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      o[e] = stencil(a, e == 0 ? left : rb[e - 1], e == V - 1 ? right : rb[e + 1], ra[e], rb[e], rc[e]);
+    if constexpr (DEAD) {
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (dead & (1u << e)) o[e] = rb[e];
+    }
+    if constexpr (ADJ) {
+      // ring cells add their link weight times the old adjacent interior value,
+      // rounded as stencil() rounds a ring cell's chain: the row-0 (y+1 link),
+      // column-0 (x+1 link) and column nx+1 (x-1 link) cells add it in one
+      // fused multiply-add after the centre term; the row ny+1 cell's link
+      // (y-1) is the chain's leading product, rounded before the add
+      if (rg.ring) {
+        if (r == 0 && (rg.ring & (1 << SIDE_YM))) {
+#pragma unroll
+          for (int e = 0; e < V; ++e) rg.ym[e] = fma_rn(rg.S, rb[e], rg.ym[e]);
+        }
+        if (r == rows - 1 && (rg.ring & (1 << SIDE_YP))) {
+#pragma unroll
+          for (int e = 0; e < V; ++e) rg.yp[e] = add_rn(rg.yp[e], mul_rn(rg.N, rb[e]));
+        }
+        if (rg.ring & (1 << SIDE_XM)) {
+          const T c0 = __shfl_sync(0xffffffffu, rb[0], 0);
+          if (lane == (r & 31)) {
+            if (r < 32) rg.xm0 = fma_rn(rg.W, c0, rg.xm0);
+            else rg.xm1 = fma_rn(rg.W, c0, rg.xm1);
+          }
+        }
+        if (rg.ring & (1 << SIDE_XP)) {
+          T ce = rb[0];
+#pragma unroll
+          for (int e = 1; e < V; ++e)
+            if (rg.xp_elem == e) ce = rb[e];
+          const T cx = __shfl_sync(0xffffffffu, ce, rg.xp_lane & 31);
+          if (lane == (r & 31)) {
+            if (r < 32) rg.xp0 = fma_rn(rg.E, cx, rg.xp0);
+            else rg.xp1 = fma_rn(rg.E, cx, rg.xp1);
+          }
+        }
+      }
+    }
+    vstore(drow + r * SW, o);
+#pragma unroll
+    for (int e = 0; e < V; ++e) { ra[e] = rb[e]; rb[e] = rc[e]; }
+  }
+}
+
+// Advance one strip by k steps: load, exchange, sweep, store.  Called by
+// every warp of the CTA with the same k (inactive strips only take part in
+// the per-step CTA barrier).  Exchange protocol: the four edge mailboxes of a
+// strip are double-buffered by step parity; in step t a strip reads parity
+// t&1 and writes its new edges into its neighbours' parity (t+1)&1.  One CTA
+// barrier per step orders this for neighbours in the same CTA; a neighbour
+// in another CTA is ordered by its published step counter (release/acquire
+// at GPU scope), waited for only by the strips that border it.
 template <typename T, bool ADJ>
 __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int warp, int slot, int src, int dst,
                           int k, int base, uint32_t &mbar_phase) {
@@ -195,8 +287,8 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
   T *data = wbase + (size_t)warp * region;
   T *mbox = data + (size_t)kp.rmax * SW;  // my shared-memory mailboxes
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-  int *sflags = reinterpret_cast<int *>(smem + 512);
-  const GridDev &gd = kp.grids[st.g];
+  const bool act = st.active;
+  const GridDev &gd = kp.grids[act ? st.g : 0];
   const int nx = gd.nx, ny = gd.ny, rows = st.rows;
   const long pitch = gd.pitch;
   const int off = gd.off;
@@ -213,222 +305,167 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
   const Links<T> a = ADJ ? Links<T>{E, W, N, C, S} : Links<T>{W, E, S, C, N};
 
   // where my incoming halos live (per side) and where my outgoing edges go
-  bool in_global[4], out_global[4], any_remote = false;
+  bool remote[4], any_remote = false;
   const T *inbox[4];
   T *outbox[4];
-  const int *nflag[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    const int n = st.link[s];
-    const bool remote = n >= 0 && (n / NW) != (slot / NW);
-    in_global[s] = remote;
-    out_global[s] = remote;
-    any_remote |= remote;
-    inbox[s] = remote ? gslots + (size_t)slot * slot_elems + L::side_off(s, rp) : mbox + L::side_off(s, rp);
+    const int n = act ? st.link[s] : LINK_ZERO;
+    remote[s] = n >= 0 && (n / NW) != (slot / NW);
+    any_remote |= remote[s];
+    inbox[s] = remote[s] ? gslots + (size_t)slot * slot_elems + L::side_off(s, rp) : mbox + L::side_off(s, rp);
     const int opp = s ^ 1;
-    if (n >= 0) {
-      outbox[s] = remote ? gslots + (size_t)n * slot_elems + L::side_off(opp, rp)
-                         : wbase + (size_t)(n % NW) * region + (size_t)kp.rmax * SW + L::side_off(opp, rp);
-      nflag[s] = remote ? kp.gflags + n : sflags + (n % NW);
-    } else {
-      outbox[s] = nullptr;
-      nflag[s] = nullptr;
-    }
+    outbox[s] = n < 0 ? nullptr
+                      : remote[s] ? gslots + (size_t)n * slot_elems + L::side_off(opp, rp)
+                                  : wbase + (size_t)(n % NW) * region + (size_t)kp.rmax * SW + L::side_off(opp, rp);
   }
+  auto publish_remote = [&](int value) {
+    if (!any_remote) return;
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) st_relaxed_gpu(kp.gflags + slot, value);
+    __syncwarp();
+  };
 
-  // ---- load the strip (TMA) ----
-  fence_proxy_async_all();  // earlier generic writes (this warp's and, via the barriers, other CTAs') before async reads
-  __syncwarp();
-  if (lane == 0) {
-    bulk_wait_read_all();  // previous strip's stores have read shared memory
-    mbar_expect_tx(&bars[warp], (uint32_t)(SW * kp.rmax * sizeof(T)));
-    tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
-  }
-  // constant halos (ring in the forward map, overlapped-halo edge rows/columns)
   const int xl = st.x0 + lane * V;  // logical x of this lane's element 0
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (st.link[s] >= 0) continue;
-    // the adjoint never reads ring cells (their links to the interior are removed)
-    const bool zero = st.link[s] == LINK_ZERO || (ADJ && ((st.ring >> s) & 1));
-    T *box = mbox + L::side_off(s, rp);
-    const int len = L::side_len(s, rp);
-    if (s <= SIDE_YP) {
-      const int y = s == SIDE_YM ? st.y0 - 1 : st.y0 + rows;
-      T v[V];
-#pragma unroll
-      for (int e = 0; e < V; ++e) {
-        const int x = xl + e;
-        v[e] = (!zero && x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
-      }
-      vstore(box + lane * V, v);
-      vstore(box + len + lane * V, v);
-    } else {
-      const int x = s == SIDE_XM ? st.x0 - 1 : st.x0 + SW;
-      for (int r = lane; r < rows; r += 32) {
-        const int y = st.y0 + r;
-        const T v = (!zero && x >= 0 && x <= nx + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
-        box[r] = v;
-        box[len + r] = v;
-      }
-    }
-  }
-  // adjoint ring accumulators start from the ring values of the source
-  T acc_ym[V], acc_yp[V], acc_xm0 = 0, acc_xm1 = 0, acc_xp0 = 0, acc_xp1 = 0;
-#pragma unroll
-  for (int e = 0; e < V; ++e) { acc_ym[e] = T(0); acc_yp[e] = T(0); }
-  if (ADJ) {
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-      const int x = xl + e;
-      const bool xin = x >= 1 && x <= nx;
-      if ((st.ring & (1 << SIDE_YM)) && xin) acc_ym[e] = srcbuf[off + x];
-      if ((st.ring & (1 << SIDE_YP)) && xin) acc_yp[e] = srcbuf[(long)(ny + 1) * pitch + off + x];
-    }
-    if (st.ring & (1 << SIDE_XM)) {
-      if (lane < rows) acc_xm0 = srcbuf[(long)(st.y0 + lane) * pitch + off];
-      if (lane + 32 < rows) acc_xm1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off];
-    }
-    if (st.ring & (1 << SIDE_XP)) {
-      if (lane < rows) acc_xp0 = srcbuf[(long)(st.y0 + lane) * pitch + off + nx + 1];
-      if (lane + 32 < rows) acc_xp1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1];
-    }
-  }
+  T *drow = data + lane * V;        // this lane's vector in strip row 0
   // columns beyond nx are dead: they keep their value (the ring column nx+1
   // is read by column nx: the ring value forward, zero in the adjoint)
   uint32_t dead = 0;
 #pragma unroll
   for (int e = 0; e < V; ++e)
-    if (xl + e > nx) dead |= 1u << e;
-  // the element holding column nx, for the adjoint right-ring accumulation
-  const int xp_lane = (nx - st.x0) / V, xp_elem = (nx - st.x0) % V;
-
-  wait_mbar(&bars[warp], mbar_phase, kp);
-  mbar_phase ^= 1u;
-  if (ADJ && dead) {
+    if (act && xl + e > nx) dead |= 1u << e;
+  // adjoint ring accumulators; the element holding column nx feeds the right ring
+  RingAcc<T> rg;
 #pragma unroll
-    for (int e = 0; e < V; ++e)
-      if (xl + e == nx + 1)
-        for (int r = 0; r < rows; ++r) data[r * SW + lane * V + e] = T(0);
-  }
-  __syncwarp();
-
-  // ---- publish state-0 edges ----
-  auto publish_edges = [&](int par, int r, const T *o) {
-    if (r == 0 && outbox[SIDE_YM]) vstore(outbox[SIDE_YM] + par * SW + lane * V, o);
-    if (r == rows - 1 && outbox[SIDE_YP]) vstore(outbox[SIDE_YP] + par * SW + lane * V, o);
-    if (lane == 0 && outbox[SIDE_XM]) outbox[SIDE_XM][par * rp + r] = o[0];
-    if (lane == 31 && outbox[SIDE_XP]) outbox[SIDE_XP][par * rp + r] = o[V - 1];
+  for (int e = 0; e < V; ++e) { rg.ym[e] = T(0); rg.yp[e] = T(0); }
+  rg.xm0 = rg.xm1 = rg.xp0 = rg.xp1 = T(0);
+  rg.ring = ADJ && act ? st.ring : 0;
+  rg.xp_lane = (nx - st.x0) / V;
+  rg.xp_elem = (nx - st.x0) % V;
+  rg.W = W; rg.E = E; rg.S = S; rg.N = N;
+  // copy this strip's current edges into the neighbours' mailboxes of parity `par`
+  auto publish_edges = [&](int par) {
+    if (outbox[SIDE_YM]) {
+      T o[V];
+      vload(drow, false, o);
+      vstore(outbox[SIDE_YM] + par * SW + lane * V, o);
+    }
+    if (outbox[SIDE_YP]) {
+      T o[V];
+      vload(drow + (rows - 1) * SW, false, o);
+      vstore(outbox[SIDE_YP] + par * SW + lane * V, o);
+    }
+    if (outbox[SIDE_XM])
+      for (int r = lane; r < rows; r += 32) outbox[SIDE_XM][par * rp + r] = data[r * SW];
+    if (outbox[SIDE_XP])
+      for (int r = lane; r < rows; r += 32) outbox[SIDE_XP][par * rp + r] = data[r * SW + SW - 1];
   };
-  auto publish_flag = [&](int value) {
-    if (any_remote) fence_acq_rel_gpu(); else fence_acq_rel_cta();
+
+  if (act) {
+    // ---- load the strip (TMA) ----
+    fence_proxy_async_all();  // earlier generic writes before the async-proxy load
     __syncwarp();
     if (lane == 0) {
-      st_relaxed_cta(sflags + warp, value);
-      if (any_remote) st_relaxed_gpu(kp.gflags + slot, value);
+      bulk_wait_read_all();  // previous strip's stores have read shared memory
+      mbar_expect_tx(&bars[warp], (uint32_t)(SW * kp.rmax * sizeof(T)));
+      tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
     }
-    __syncwarp();
-  };
-  for (int r = 0; r < rows; ++r) {
-    if (r != 0 && r != rows - 1 && !outbox[SIDE_XM] && !outbox[SIDE_XP]) continue;
-    T o[V];
-    vload(data + r * SW + lane * V, false, o);
-    publish_edges(0, r, o);
-  }
-  publish_flag(base);
-
-  // ---- k steps ----
-  for (int t = 0; t < k; ++t) {
-    const int par = t & 1;
+    // constant halos (ring in the forward map, overlapped-halo edge rows/columns)
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (nflag[s]) wait_flag(nflag[s], in_global[s], base + t, kp);
-    // halos of state t
-    T hym[V], hyp[V];
-    vload(inbox[SIDE_YM] + par * L::side_len(SIDE_YM, rp) + lane * V, in_global[SIDE_YM], hym);
-    vload(inbox[SIDE_YP] + par * L::side_len(SIDE_YP, rp) + lane * V, in_global[SIDE_YP], hyp);
-    T hxm0 = 0, hxm1 = 0, hxp0 = 0, hxp1 = 0;
-    {
-      const T *bx = inbox[SIDE_XM] + par * rp;
-      const T *bp = inbox[SIDE_XP] + par * rp;
-      if (lane < rows) {
-        hxm0 = in_global[SIDE_XM] ? ld_cg(bx + lane) : bx[lane];
-        hxp0 = in_global[SIDE_XP] ? ld_cg(bp + lane) : bp[lane];
-      }
-      if (lane + 32 < rows) {
-        hxm1 = in_global[SIDE_XM] ? ld_cg(bx + lane + 32) : bx[lane + 32];
-        hxp1 = in_global[SIDE_XP] ? ld_cg(bp + lane + 32) : bp[lane + 32];
-      }
-    }
-    // sweep rows top to bottom with a three-row window, updating in place
-    T prv[V], cur[V], nxt[V];
+    for (int s = 0; s < 4; ++s) {
+      if (st.link[s] >= 0) continue;
+      // the adjoint never reads ring cells (their links to the interior are removed)
+      const bool zero = st.link[s] == LINK_ZERO || (ADJ && ((st.ring >> s) & 1));
+      T *box = mbox + L::side_off(s, rp);
+      const int len = L::side_len(s, rp);
+      if (s <= SIDE_YP) {
+        const int y = s == SIDE_YM ? st.y0 - 1 : st.y0 + rows;
+        T v[V];
 #pragma unroll
-    for (int e = 0; e < V; ++e) prv[e] = hym[e];
-    vload(data + lane * V, false, cur);
-    for (int r = 0; r < rows; ++r) {
-      if (r + 1 < rows) {
-        vload(data + (r + 1) * SW + lane * V, false, nxt);
+        for (int e = 0; e < V; ++e) {
+          const int x = xl + e;
+          v[e] = (!zero && x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+        }
+        vstore(box + lane * V, v);
+        vstore(box + len + lane * V, v);
       } else {
-#pragma unroll
-        for (int e = 0; e < V; ++e) nxt[e] = hyp[e];
+        const int x = s == SIDE_XM ? st.x0 - 1 : st.x0 + SW;
+        for (int r = lane; r < rows; r += 32) {
+          const int y = st.y0 + r;
+          const T v = (!zero && x >= 0 && x <= nx + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+          box[r] = v;
+          box[len + r] = v;
+        }
       }
-      T left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
-      T right = __shfl_down_sync(0xffffffffu, cur[0], 1);
-      const T hl = __shfl_sync(0xffffffffu, r < 32 ? hxm0 : hxm1, r & 31);
-      const T hr = __shfl_sync(0xffffffffu, r < 32 ? hxp0 : hxp1, r & 31);
-      if (lane == 0) left = hl;
-      if (lane == 31) right = hr;
-      T o[V];
+    }
+    // adjoint ring accumulators start from the ring values of the source
+    if (ADJ) {
 #pragma unroll
       for (int e = 0; e < V; ++e) {
-        const T xm = e == 0 ? left : cur[e - 1];
-        const T xp = e == V - 1 ? right : cur[e + 1];
-        o[e] = stencil(a, xm, xp, prv[e], cur[e], nxt[e]);
+        const int x = xl + e;
+        const bool xin = x >= 1 && x <= nx;
+        if ((st.ring & (1 << SIDE_YM)) && xin) rg.ym[e] = srcbuf[off + x];
+        if ((st.ring & (1 << SIDE_YP)) && xin) rg.yp[e] = srcbuf[(long)(ny + 1) * pitch + off + x];
       }
-      if (dead) {
-#pragma unroll
-        for (int e = 0; e < V; ++e)
-          if (dead & (1u << e)) o[e] = cur[e];
+      if (st.ring & (1 << SIDE_XM)) {
+        if (lane < rows) rg.xm0 = srcbuf[(long)(st.y0 + lane) * pitch + off];
+        if (lane + 32 < rows) rg.xm1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off];
       }
-      if (ADJ && st.ring) {
-        // ring cells add their link weight times the old adjacent interior value,
-        // rounded as the one-step kernel's link chain does: the y+1 link of the
-        // bottom ring row is its last term (one fused multiply-add), the other
-        // ring sides round the product before adding it
-        if ((st.ring & (1 << SIDE_YM)) && r == 0) {
-#pragma unroll
-          for (int e = 0; e < V; ++e) acc_ym[e] = fma_rn(S, cur[e], acc_ym[e]);
-        }
-        if ((st.ring & (1 << SIDE_YP)) && r == rows - 1) {
-#pragma unroll
-          for (int e = 0; e < V; ++e) acc_yp[e] = add_rn(acc_yp[e], mul_rn(N, cur[e]));
-        }
-        if (st.ring & (1 << SIDE_XM)) {
-          const T c0 = __shfl_sync(0xffffffffu, cur[0], 0);
-          if (lane == (r & 31)) {
-            if (r < 32) acc_xm0 = add_rn(acc_xm0, mul_rn(W, c0));
-            else acc_xm1 = add_rn(acc_xm1, mul_rn(W, c0));
-          }
-        }
-        if (st.ring & (1 << SIDE_XP)) {
-          T ce = cur[0];
-#pragma unroll
-          for (int e = 1; e < V; ++e)
-            if (xp_elem == e) ce = cur[e];
-          const T cx = __shfl_sync(0xffffffffu, ce, xp_lane & 31);
-          if (lane == (r & 31)) {
-            if (r < 32) acc_xp0 = add_rn(acc_xp0, mul_rn(E, cx));
-            else acc_xp1 = add_rn(acc_xp1, mul_rn(E, cx));
-          }
-        }
+      if (st.ring & (1 << SIDE_XP)) {
+        if (lane < rows) rg.xp0 = srcbuf[(long)(st.y0 + lane) * pitch + off + nx + 1];
+        if (lane + 32 < rows) rg.xp1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1];
       }
-      vstore(data + r * SW + lane * V, o);
-      publish_edges(par ^ 1, r, o);
-#pragma unroll
-      for (int e = 0; e < V; ++e) { prv[e] = cur[e]; cur[e] = nxt[e]; }
     }
-    publish_flag(base + t + 1);
+    wait_mbar(&bars[warp], mbar_phase, kp);
+    mbar_phase ^= 1u;
+    if (ADJ && dead) {
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (xl + e == nx + 1)
+          for (int r = 0; r < rows; ++r) drow[r * SW + e] = T(0);
+    }
+    __syncwarp();
+    // ---- publish state-0 edges into the neighbours' parity-0 mailboxes ----
+    publish_edges(0);
+    publish_remote(base);
   }
+  __syncthreads();
+
+  // ---- k steps ----
+  // lane 0 reads the x-1 halo column, lane 31 the x+1 one (other lanes: any)
+  const int hside = lane == 31 ? SIDE_XP : SIDE_XM;
+  const bool any_dead = __any_sync(0xffffffffu, dead != 0);
+  for (int t = 0; t < k; ++t) {
+    if (act) {
+      const int par = t & 1;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (remote[s]) wait_flag(kp.gflags + st.link[s], true, base + t, kp);
+      // halos of state t: rows into registers; remote columns staged into shared memory
+      T hym[V], hyp[V];
+      vload(inbox[SIDE_YM] + par * SW + lane * V, remote[SIDE_YM], hym);
+      vload(inbox[SIDE_YP] + par * SW + lane * V, remote[SIDE_YP], hyp);
+#pragma unroll
+      for (int s = SIDE_XM; s <= SIDE_XP; ++s) {
+        if (!remote[s]) continue;
+        T *sb = mbox + L::side_off(s, rp) + par * rp;
+        const T *gb = inbox[s] + par * rp;
+        for (int r = lane; r < rows; r += 32) sb[r] = ld_cg(gb + r);
+      }
+      __syncwarp();
+      const T *hcol = mbox + L::side_off(hside, rp) + par * rp;
+      if (any_dead)
+        sweep_rows<T, ADJ, true>(drow, hcol, rows, lane, a, hym, hyp, dead, rg);
+      else
+        sweep_rows<T, ADJ, false>(drow, hcol, rows, lane, a, hym, hyp, dead, rg);
+      __syncwarp();
+      publish_edges(par ^ 1);
+      publish_remote(base + t + 1);
+    }
+    __syncthreads();
+  }
+  if (!act) return;
 
   // ---- store the valid part ----
   const bool full = st.sx0 == 0 && st.sx1 == SW;
@@ -463,19 +500,19 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
     for (int e = 0; e < V; ++e) {
       const int c = lane * V + e, x = st.x0 + c;
       const bool xin = x >= 1 && x <= nx && c >= st.sx0 && c < st.sx1;
-      if ((st.ring & (1 << SIDE_YM)) && xin && st.sy0 == 0) dstbuf[off + x] = acc_ym[e];
-      if ((st.ring & (1 << SIDE_YP)) && xin && st.sy1 == rows) dstbuf[(long)(ny + 1) * pitch + off + x] = acc_yp[e];
+      if ((st.ring & (1 << SIDE_YM)) && xin && st.sy0 == 0) dstbuf[off + x] = rg.ym[e];
+      if ((st.ring & (1 << SIDE_YP)) && xin && st.sy1 == rows) dstbuf[(long)(ny + 1) * pitch + off + x] = rg.yp[e];
     }
     if ((st.ring & (1 << SIDE_XM)) && st.sx0 == 0) {
-      if (lane < rows && lane >= st.sy0 && lane < st.sy1) dstbuf[(long)(st.y0 + lane) * pitch + off] = acc_xm0;
+      if (lane < rows && lane >= st.sy0 && lane < st.sy1) dstbuf[(long)(st.y0 + lane) * pitch + off] = rg.xm0;
       if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
-        dstbuf[(long)(st.y0 + lane + 32) * pitch + off] = acc_xm1;
+        dstbuf[(long)(st.y0 + lane + 32) * pitch + off] = rg.xm1;
     }
     if ((st.ring & (1 << SIDE_XP)) && (nx - st.x0) < st.sx1) {
       if (lane < rows && lane >= st.sy0 && lane < st.sy1)
-        dstbuf[(long)(st.y0 + lane) * pitch + off + nx + 1] = acc_xp0;
+        dstbuf[(long)(st.y0 + lane) * pitch + off + nx + 1] = rg.xp0;
       if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
-        dstbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1] = acc_xp1;
+        dstbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1] = rg.xp1;
     }
   }
 }
@@ -554,6 +591,31 @@ __device__ Strip tile_strip(const KParams &kp, const int *tile, int w, int cta_s
   return st;
 }
 
+// Ring copy for every grid of a run in one launch: block (g, d) copies the
+// ring of grid g's input to its buffer d (1 = workspace, 2 = output).
+template <typename T>
+__global__ void ring_copy_grids_kernel(const GridDev *grids, int copy_ws, int copy_out) {
+  const GridDev &g = grids[blockIdx.x];
+  const int d = blockIdx.y == 0 ? 2 : 1;
+  if ((d == 2 && !copy_out) || (d == 1 && !copy_ws) || g.buf[d] == g.buf[0]) return;
+  const T *in = reinterpret_cast<const T *>(g.buf[0]);
+  T *out = reinterpret_cast<T *>(g.buf[d]);
+  const int nx = g.nx, ny = g.ny, n_rows = 2 * (nx + 2), n = n_rows + 2 * ny;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int y, x;
+    if (i < n_rows) {
+      y = (i < nx + 2) ? 0 : ny + 1;
+      x = i % (nx + 2);
+    } else {
+      const int j = i - n_rows;
+      y = 1 + (j >> 1);
+      x = (j & 1) ? nx + 1 : 0;
+    }
+    const long e = (long)y * g.pitch + g.off + x;
+    out[e] = in[e];
+  }
+}
+
 template <typename T, bool ADJ, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant__ KParams kp) {
   constexpr int SWc = 32 * VecOf<T>::V;
@@ -580,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
     if (MODE == MODE_BANDS) {
       for (int wv = 0; wv < kp.njobs; ++wv, ++seq) {
         const Strip st = band_strip(kp, kp.jobs + 5 * wv, slot, SWc);
-        if (st.active) run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
         if (lane == 0) {
           bulk_wait_all();
           fence_proxy_async_global();
@@ -590,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
     } else {
       for (int j = blockIdx.x; j < kp.njobs; j += gridDim.x, ++seq) {
         const Strip st = tile_strip(kp, kp.jobs + 7 * j, warp, blockIdx.x * kWarps, SWc);
-        if (st.active) run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
         __syncthreads();
       }
       if (lane == 0) {
@@ -747,8 +809,8 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
       if (ncs > slots) { err = "grid too wide for one band"; return cudaErrorNotSupported; }
       const int m = (int)std::min<long>(slots / ncs, g.ny);
       const int hb = m * rmax;
-      if (hb <= 2 * depth) { err = "band too short for the temporal depth"; return cudaErrorNotSupported; }
       auto cv = cover(g.ny, hb, depth);
+      if (cv.empty() || cv.back() != g.ny + 1) { err = "band too short for the temporal depth"; return cudaErrorNotSupported; }
       for (size_t i = 0; i + 2 < cv.size(); i += 3) {
         const int bs = cv[i], ve = cv[i + 2];
         const int be = std::min(g.ny + 1, bs + hb);
@@ -760,10 +822,15 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
       const int trows = rmax;
       const int tw = wx * SW, th = wy * trows;
       const int gx = (depth + V - 1) / V * V;
-      if (tw <= 2 * gx || th <= 2 * depth) { err = "tile too small for the temporal depth"; return cudaErrorNotSupported; }
       for (size_t gi = 0; gi < grids.size(); ++gi) {
         const GridDesc &g = grids[gi];
+        // a grid that fits one tile needs no overlapped halo; otherwise the
+        // halo of depth k must leave each tile a valid core
         auto cx = cover(g.nx, tw, gx), cy = cover(g.ny, th, depth);
+        if (cx.back() != g.nx + 1 || cy.back() != g.ny + 1) {
+          err = "tile too small for the temporal depth";
+          return cudaErrorNotSupported;
+        }
         for (size_t a = 0; a + 2 < cy.size(); a += 3)
           for (size_t b = 0; b + 2 < cx.size(); b += 3)
             jobs.insert(jobs.end(), {(int)gi, cx[b], cy[a], cx[b + 1], cx[b + 2], cy[a + 1], cy[a + 2]});
@@ -825,9 +892,14 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   // ring of every buffer a round writes = ring of the input (constant forward;
   // corners and the starting values of the adjoint ring accumulation)
   int src0 = 0;
-  for (size_t i = 0; i < ng; ++i) {
-    if (r.out[i] != r.in[i] && (e = launch_ring_copy(dt, r.in[i], r.out[i], grids[i], s)) != cudaSuccess) return e;
-    if (rounds > 1 && (e = launch_ring_copy(dt, r.in[i], r.ws[i], grids[i], s)) != cudaSuccess) return e;
+  {
+    const GridDev *gd = reinterpret_cast<const GridDev *>(S.desc);
+    note_launch();
+    if (dt == J2D_F64)
+      ring_copy_grids_kernel<double><<<dim3((unsigned)ng, 2), 256, 0, s>>>(gd, rounds > 1, 1);
+    else
+      ring_copy_grids_kernel<float><<<dim3((unsigned)ng, 2), 256, 0, s>>>(gd, rounds > 1, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) { err = "ring copy"; return e; }
   }
   // overlapped halos read neighbours' cells: a round must not write its source
   const int dst0 = ((rounds - 1) & 1) == 0 ? 2 : 1;
