@@ -141,6 +141,25 @@ j2d_status j2d5pt_run_adjoint(j2d5pt_plan_t plan, const void *lam_T, void *lam_0
 j2d_status j2d5pt_weight_grad(j2d5pt_plan_t plan, const void *u_t, const void *lam_t1,
                               double *dw, void *stream);
 
+/* Same reduction for callers that cannot allocate device memory; no plan
+ * needed.  (The paper has no counterpart: this is a deployment variant.)
+ * Callers that cannot call cudaMalloc: code running while a stream is being
+ * captured into a CUDA graph, code whose device memory is owned by a
+ * framework's caching allocator, and latency-bound loops that cannot absorb
+ * cudaFree's device-wide synchronisation.  Allocates nothing: its scratch (the
+ * per-block partial sums) is a fixed 2.5 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * u_t and lam_t1 are nx*ny grids in the plan layout j2d5pt_plan would give for
+ * (nx, ny, dtype); dw as for j2d5pt_weight_grad (accumulated).  Grids needing
+ * more than 65536 partial-sum blocks (about 1.3e8 FP64 or 2.7e8 FP32 cells)
+ * are rejected with J2D_ERR_ARG.  The first call on each device looks up the
+ * array's device address (once, with that device current); make it before
+ * any stream capture.  All calls share the one array: calls that overlap on
+ * the GPU (other streams, other threads) race and give wrong results;
+ * serialise them.  Asynchronous on `stream`. */
+j2d_status j2d5pt_weight_grad_noalloc(int nx, int ny, j2d_dtype dtype, const void *u_t,
+                                      const void *lam_t1, double *dw, void *stream);
+
 /* ---- status, tuning, diagnostics ---------------------------------------- */
 
 /* Synchronise the stream of the plan's last run and return its device-side

@@ -27,6 +27,18 @@ static j2d_status fail(j2d_status st, const char *fmt, ...) {
   g_last_error = buf;
   return st;
 }
+namespace j2d {
+j2d_status record_error(j2d_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+}  // namespace j2d
+
 static j2d_status cuda_fail(cudaError_t e, const char *what) {
   return fail(J2D_ERR_DEVICE, "%s: %s", what, cudaGetErrorString(e));
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,9 @@ struct DtbScratch {
   void *base = nullptr;
   size_t bytes = 0;
 };
+
+// Record a message for j2d5pt_last_error() on this thread; returns `st`.
+j2d_status record_error(j2d_status st, const char *fmt, ...);
 
 // Count of kernels launched by the library (j2d5pt_kernel_launches).
 extern std::atomic<long> g_launches;

@@ -61,6 +61,7 @@ def load():
         "j2d5pt_autotune": [P, P, P, L, P],
         "j2d5pt_autotune_batched": [P, P, P, L, P],
         "j2d5pt_measure_fma_rate": [I, ctypes.POINTER(D)],
+        "j2d5pt_weight_grad_noalloc": [I, I, I, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -173,6 +174,11 @@ def j2d5pt_run_adjoint(h, lam_T, lam_0, steps, stream=None):
 
 def j2d5pt_weight_grad(h, u_t, lam_t1, dw, stream=None):
     _check(load().j2d5pt_weight_grad(h, _ptr(u_t), _ptr(lam_t1), _ptr(dw), _stream_ptr(stream)))
+
+
+def j2d5pt_weight_grad_noalloc(nx, ny, dtype, u_t, lam_t1, dw, stream=None):
+    _check(load().j2d5pt_weight_grad_noalloc(int(nx), int(ny), int(dtype), _ptr(u_t), _ptr(lam_t1), _ptr(dw),
+                                             _stream_ptr(stream)))
 
 
 def j2d5pt_sync_status(h):
