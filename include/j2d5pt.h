@@ -75,7 +75,9 @@ typedef enum {
   J2D_OPT_TILE_WX = 2,    /* TILES: warp strips across a CTA tile (16 / WX down) */
   J2D_OPT_CTAS = 3,       /* persistent grid size (0 = one CTA per SM) */
   J2D_OPT_TIMEOUT_MS = 4, /* device-side wait limit in milliseconds (default 2000) */
-  J2D_OPT_VERBOSE = 5     /* 1 = print the chosen configuration to stderr at run time */
+  J2D_OPT_VERBOSE = 5,    /* 1 = print the chosen configuration to stderr at run time */
+  J2D_OPT_GRAPH = 6       /* 1 = forward runs are captured into a CUDA graph on first use (per
+                             buffers and step count) and replayed by later identical calls */
 } j2d_option;
 
 /* ---- plans ------------------------------------------------------------- */
@@ -92,6 +94,10 @@ j2d_status j2d5pt_plan_batched(j2d5pt_plan_t *plan, int count, const int *nx, co
                                j2d_dtype dtype, const double *weights);
 
 j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t plan);
+
+/* Replace the weights {W, E, S, C, N} of grid `index` (host, FP64).  Later
+ * runs use them; a graph captured under J2D_OPT_GRAPH is discarded. */
+j2d_status j2d5pt_set_weights(j2d5pt_plan_t plan, int index, const double weights[5]);
 
 /* Layout of grid `index` (0 for single-grid plans): elements per row and the
  * element offset of logical column 0 (see the layout rules above). */

@@ -65,7 +65,22 @@ struct j2d5pt_plan_s {
   DtbState dtb;
   cudaStream_t last_stream = nullptr;
   bool ran = false;
+  // CUDA graph of the last forward run (J2D_OPT_GRAPH)
+  int opt_graph = 0;
+  std::vector<const void *> g_in;
+  std::vector<void *> g_out;
+  long g_steps = -1;
+  cudaGraphExec_t g_exec = nullptr;
+  cudaStream_t g_stream = nullptr;
 };
+
+static void drop_graph(j2d5pt_plan_t p) {
+  if (p->g_exec) cudaGraphExecDestroy(p->g_exec);
+  p->g_exec = nullptr;
+  p->g_in.clear();
+  p->g_out.clear();
+  p->g_steps = -1;
+}
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -133,6 +148,8 @@ extern "C" j2d_status j2d5pt_plan_batched(j2d5pt_plan_t *plan, int count, const 
 extern "C" j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t p) {
   if (!p) return fail(J2D_ERR_ARG, "destroy: null plan");
   if (p->ran && p->last_stream) cudaStreamSynchronize(p->last_stream);
+  drop_graph(p);
+  if (p->g_stream) cudaStreamDestroy(p->g_stream);
   dtb_release(p->dtb);
   cudaFree(p->ws);
   cudaFree(p->partials);
@@ -140,6 +157,16 @@ extern "C" j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t p) {
   cudaFree(p->h_in_dev);
   cudaFree(p->h_out_dev);
   delete p;
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_set_weights(j2d5pt_plan_t p, int index, const double *w) {
+  if (!p || !w) return fail(J2D_ERR_ARG, "set_weights: null argument");
+  if (index < 0 || index >= (int)p->grids.size()) return fail(J2D_ERR_ARG, "set_weights: index %d out of range", index);
+  for (int d = 0; d < 5; ++d)
+    if (!std::isfinite(w[d])) return fail(J2D_ERR_ARG, "set_weights: weight %d is not finite", d);
+  for (int d = 0; d < 5; ++d) p->grids[index].w[d] = p->dtype == J2D_F64 ? w[d] : (double)(float)w[d];
+  drop_graph(p);
   return J2D_OK;
 }
 
@@ -157,15 +184,18 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
     case J2D_OPT_ALGO:
       if (v < J2D_ALGO_AUTO || v > J2D_ALGO_TILES) return fail(J2D_ERR_ARG, "set_option: bad algo %ld", v);
       p->opt_algo = (int)v;
+      drop_graph(p);
       break;
     case J2D_OPT_DEPTH:
       if (v < 0 || v > 256) return fail(J2D_ERR_ARG, "set_option: depth %ld outside 0..256", v);
       p->opt_depth = (int)v;
+      drop_graph(p);
       break;
     case J2D_OPT_TILE_WX:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8 && v != 16)
         return fail(J2D_ERR_ARG, "set_option: tile_wx must be 0, 1, 2, 4, 8 or 16");
       p->opt_tile_wx = (int)v;
+      drop_graph(p);
       break;
     case J2D_OPT_CTAS:
       if (v < 0 || v > 65535) return fail(J2D_ERR_ARG, "set_option: ctas %ld", v);
@@ -177,6 +207,10 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
       break;
     case J2D_OPT_VERBOSE:
       p->opt_verbose = (int)v;
+      break;
+    case J2D_OPT_GRAPH:
+      p->opt_graph = v != 0;
+      drop_graph(p);
       break;
     default:
       return fail(J2D_ERR_ARG, "set_option: unknown option %d", (int)opt);
@@ -193,6 +227,7 @@ extern "C" j2d_status j2d5pt_get_option(j2d5pt_plan_t p, j2d_option opt, long *v
     case J2D_OPT_CTAS: *v = p->opt_ctas; break;
     case J2D_OPT_TIMEOUT_MS: *v = p->opt_timeout_ms; break;
     case J2D_OPT_VERBOSE: *v = p->opt_verbose; break;
+    case J2D_OPT_GRAPH: *v = p->opt_graph; break;
     default: return fail(J2D_ERR_ARG, "get_option: unknown option %d", (int)opt);
   }
   return J2D_OK;
@@ -302,16 +337,62 @@ static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const
   return J2D_OK;
 }
 
+// Forward run, through a CUDA graph when J2D_OPT_GRAPH is set: the first call
+// for given buffers and step count runs normally (sizing the workspace and
+// uploading the launch descriptors), then captures the same sequence of
+// launches on a private stream; later identical calls replay the graph.
+static j2d_status run_forward(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps, cudaStream_t s) {
+  if (!p->opt_graph) return run_common(p, in, out, steps, false, s);
+  const size_t n = p->grids.size();
+  bool hit = p->g_exec && p->g_steps == steps;
+  for (size_t i = 0; hit && i < n; ++i) hit = p->g_in[i] == in[i] && p->g_out[i] == out[i];
+  cudaError_t e;
+  if (hit) {
+    if ((e = cudaGraphLaunch(p->g_exec, s)) != cudaSuccess) return cuda_fail(e, "run: graph launch");
+    p->last_stream = s;
+    p->ran = true;
+    return J2D_OK;
+  }
+  drop_graph(p);
+  j2d_status st = run_common(p, in, out, steps, false, s);
+  if (st != J2D_OK || steps == 0) return st;
+  if (!p->g_stream && (e = cudaStreamCreateWithFlags(&p->g_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "run: graph stream");
+  // the capture stream must not start before the plain run has finished with the buffers
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "run: sync before capture");
+  if ((e = cudaStreamBeginCapture(p->g_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return cuda_fail(e, "run: begin capture");
+  st = run_common(p, in, out, steps, false, p->g_stream);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(p->g_stream, &graph);
+  p->last_stream = s;
+  if (st != J2D_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "run: end capture");
+  e = cudaGraphInstantiate(&p->g_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    p->g_exec = nullptr;
+    return cuda_fail(e, "run: graph instantiate");
+  }
+  p->g_in.assign(in, in + n);
+  p->g_out.assign(out, out + n);
+  p->g_steps = steps;
+  return J2D_OK;
+}
+
 extern "C" j2d_status j2d5pt_run(j2d5pt_plan_t p, const void *in, void *out, long steps, void *stream) {
   if (!p) return fail(J2D_ERR_ARG, "run: null plan");
   if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "run: batched plan; use j2d5pt_run_batched");
-  return run_common(p, &in, &out, steps, false, (cudaStream_t)stream);
+  return run_forward(p, &in, &out, steps, (cudaStream_t)stream);
 }
 
 extern "C" j2d_status j2d5pt_run_batched(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps,
                                          void *stream) {
   if (!p || !in || !out) return fail(J2D_ERR_ARG, "run_batched: null argument");
-  return run_common(p, in, out, steps, false, (cudaStream_t)stream);
+  return run_forward(p, in, out, steps, (cudaStream_t)stream);
 }
 
 extern "C" j2d_status j2d5pt_run_adjoint(j2d5pt_plan_t p, const void *lam_T, void *lam_0, long steps, void *stream) {

@@ -763,7 +763,7 @@ static std::vector<int> cover(int n, int win, int g) {
 
 static void ensure(void *&p, size_t &cap, size_t need, cudaError_t &err) {
   if (cap >= need) return;
-  cudaFree(p);
+  if (p) cudaFree(p);
   p = nullptr;
   cap = 0;
   err = cudaMalloc(&p, need);
@@ -878,9 +878,15 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   const size_t scratch = 256 + nslots * sizeof(int) + (mode == MODE_BANDS ? nslots * slot_bytes : 0);
   ensure(S.scratch, S.scratch_bytes, scratch, e);
   if (e != cudaSuccess) { err = "scratch allocation"; return cudaErrorMemoryAllocation; }
-  if ((e = cudaMemcpyAsync(S.desc, host.data(), desc_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
-    err = "descriptor upload";
-    return e;
+  // upload the descriptors unless the device copy already holds them (a run
+  // repeated on the same buffers uploads nothing, so it can be captured into
+  // a CUDA graph after one plain run)
+  if (S.last_desc != host) {
+    if ((e = cudaMemcpyAsync(S.desc, host.data(), desc_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+      err = "descriptor upload";
+      return e;
+    }
+    S.last_desc = host;
   }
   char *sc = (char *)S.scratch;
   if ((e = cudaMemsetAsync(sc, 0, 256, s)) != cudaSuccess ||
@@ -954,5 +960,7 @@ void dtb_release(DtbState &S) {
   cudaFree(S.desc);
   S = DtbState{};
 }
+
+void dtb_invalidate(DtbState &S) { S.last_desc.clear(); }
 
 }  // namespace j2d

@@ -41,8 +41,7 @@ struct DtbState {
   size_t scratch_bytes = 0;
   void *desc = nullptr;     // grid descriptors, tensor maps, job lists
   size_t desc_bytes = 0;
-  void *host_desc = nullptr;  // pinned staging for `desc`
-  size_t host_desc_bytes = 0;
+  std::vector<char> last_desc;  // host copy of what `desc` holds
 };
 
 // Largest rows per warp strip that fit in shared memory.
@@ -52,5 +51,6 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
                      const DtbRequest &rq);
 cudaError_t dtb_run(DtbState &st, const DtbRun &r, cudaStream_t s, std::string &err);
 void dtb_release(DtbState &st);
+void dtb_invalidate(DtbState &st);  // forget the uploaded descriptors (weights changed)
 
 }  // namespace j2d

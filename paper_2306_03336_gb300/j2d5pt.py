@@ -20,7 +20,7 @@ J2D_F64, J2D_F32 = 0, 1
 J2D_OK, J2D_ERR_ARG, J2D_ERR_ALIGN, J2D_ERR_NOMEM, J2D_ERR_DEVICE = 0, 1, 2, 3, 4
 J2D_ERR_UNSUPPORTED, J2D_ERR_TIMEOUT, J2D_ERR_BOUNDS = 5, 6, 7
 ALGO = {"auto": 0, "onestep": 1, "resident": 2, "bands": 3, "tiles": 4}
-OPT = {"algo": 0, "depth": 1, "tile_wx": 2, "ctas": 3, "timeout_ms": 4, "verbose": 5}
+OPT = {"algo": 0, "depth": 1, "tile_wx": 2, "ctas": 3, "timeout_ms": 4, "verbose": 5, "graph": 6}
 STATUS_NAMES = {0: "J2D_OK", 1: "J2D_ERR_ARG", 2: "J2D_ERR_ALIGN", 3: "J2D_ERR_NOMEM", 4: "J2D_ERR_DEVICE",
                 5: "J2D_ERR_UNSUPPORTED", 6: "J2D_ERR_TIMEOUT", 7: "J2D_ERR_BOUNDS"}
 
@@ -49,6 +49,7 @@ def load():
         "j2d5pt_plan_batched": [PP, I, P, P, I, P],
         "j2d5pt_plan_destroy": [P],
         "j2d5pt_layout": [P, I, ctypes.POINTER(L), ctypes.POINTER(L)],
+        "j2d5pt_set_weights": [P, I, P],
         "j2d5pt_set_option": [P, I, L],
         "j2d5pt_get_option": [P, I, ctypes.POINTER(L)],
         "j2d5pt_describe": [P, ctypes.c_char_p, ctypes.c_size_t],
@@ -127,6 +128,11 @@ def j2d5pt_plan_batched(nx, ny, dtype, weights):
 
 def j2d5pt_plan_destroy(h):
     _check(load().j2d5pt_plan_destroy(h))
+
+
+def j2d5pt_set_weights(h, index, weights):
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(5)
+    _check(load().j2d5pt_set_weights(h, int(index), w.ctypes.data_as(ctypes.c_void_p)))
 
 
 def j2d5pt_layout(h, index=0):
@@ -277,6 +283,11 @@ class Plan:
 
     def get(self, opt):
         return j2d5pt_get_option(self.handle, opt)
+
+    def set_weights(self, weights, i=0):
+        j2d5pt_set_weights(self.handle, i, weights)
+        self.weights[i] = np.asarray(weights, dtype=np.float64).reshape(5)
+        return self
 
     def describe(self):
         return j2d5pt_describe(self.handle)

@@ -1,0 +1,107 @@
+"""Batched grids of uneven sizes with their own weights, advanced together in
+one persistent launch, plain and captured in a CUDA graph; every grid against
+the oracle and bit for bit against the one-step kernel."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_03336_gb300 import j2d5pt, synth
+from tests.gpu_util import TOL_F64, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+SIZES = [(1, 1), (300, 200), (64, 64), (130, 7), (7, 130), (257, 331), (1024, 64), (64, 1024), (95, 95), (513, 2)]
+
+
+def _batch(sizes, dtype, steps, depth, wx, graph=False, replays=1):
+    import torch
+    w = np.stack([synth.weights(400 + i) for i in range(len(sizes))])
+    us = [synth.field(nx, ny, 500 + i) for i, (nx, ny) in enumerate(sizes)]
+    p = j2d5pt.Plan.batch(sizes, dtype, w).set("algo", "tiles").set("depth", depth).set("tile_wx", wx)
+    if graph:
+        p.set("graph", 1)
+    srcs = [p.to_device(u.astype(p.np_dtype), i) for i, u in enumerate(us)]
+    dsts = [p.empty(i) for i in range(len(sizes))]
+    for _ in range(replays):
+        for d in dsts:
+            d.zero_()
+        p.run_batched(srcs, dsts, steps)
+        p.sync()
+    outs = [p.to_host(d, i) for i, d in enumerate(dsts)]
+    p.close()
+    return us, w, outs
+
+
+@pytest.mark.parametrize("depth,wx", [(4, 2), (7, 1), (3, 4)])
+def test_batched_against_oracle(depth, wx):
+    steps = 13
+    us, w, outs = _batch(SIZES, "f64", steps, depth, wx)
+    for u, wi, got in zip(us, w, outs):
+        assert rel_err(got, oracle.run(u, wi, steps)) <= TOL_F64
+
+
+def test_batched_bitwise_equal_to_single_grid_onestep():
+    steps = 9
+    us, w, outs = _batch(SIZES, "f64", steps, 4, 2)
+    for (nx, ny), u, wi, got in zip(SIZES, us, w, outs):
+        p = j2d5pt.Plan(nx, ny, "f64", wi).set("algo", "onestep")
+        src = p.to_device(u)
+        dst = p.empty()
+        p.run(src, dst, steps)
+        assert np.array_equal(p.to_host(dst), got)
+        p.close()
+
+
+def test_batched_cuda_graph_replay():
+    steps = 10
+    _, _, plain = _batch(SIZES, "f64", steps, 4, 2)
+    _, _, graph = _batch(SIZES, "f64", steps, 4, 2, graph=True, replays=3)
+    for a, b in zip(plain, graph):
+        assert np.array_equal(a, b)
+
+
+def test_batched_workload_256_grids_sampled():
+    # the benchmark batch: 256 grids, sides uniform in [64, 1024], 200 steps;
+    # checked against the oracle on a sample of grids
+    cfg = synth.WORKLOADS["j2d5pt_f64_batch256_200"]
+    sizes = synth.batch_sizes(cfg["count"], synth.data_seed(cfg["index"]), cfg["lo"], cfg["hi"])
+    import torch
+    w = np.stack([synth.weights(synth.weight_seed(cfg["index"]) + i) for i in range(len(sizes))])
+    p = j2d5pt.Plan.batch(sizes, "f64", w).set("algo", "tiles").set("depth", 8)
+    us = [synth.field(nx, ny, synth.data_seed(cfg["index"]) + 10 + i) for i, (nx, ny) in enumerate(sizes)]
+    srcs = [p.to_device(u, i) for i, u in enumerate(us)]
+    dsts = [p.empty(i) for i in range(len(sizes))]
+    p.run_batched(srcs, dsts, cfg["steps"])
+    p.sync()
+    for i in (0, 17, 100, 255):
+        ref = oracle.run(us[i], w[i], cfg["steps"], threads=oracle.max_threads())
+        assert rel_err(p.to_host(dsts[i], i), ref) <= TOL_F64
+    p.close()
+
+
+def test_single_grid_graph_option():
+    nx, ny, steps = 200, 150, 12
+    u0 = synth.field(nx, ny, 601)
+    w = synth.weights(602)
+    p = j2d5pt.Plan(nx, ny, "f64", w).set("graph", 1)
+    src = p.to_device(u0)
+    dst = p.empty()
+    for _ in range(3):
+        dst.zero_()
+        p.run(src, dst, steps)
+        p.sync()
+        assert rel_err(p.to_host(dst), oracle.run(u0, w, steps)) <= TOL_F64
+    # new weights drop the graph
+    w2 = synth.weights(603)
+    p.set_weights(w2)
+    p.run(src, dst, steps)
+    p.sync()
+    assert rel_err(p.to_host(dst), oracle.run(u0, w2, steps)) <= TOL_F64
+    p.close()
