@@ -76,8 +76,10 @@ typedef enum {
   J2D_OPT_CTAS = 3,       /* persistent grid size (0 = one CTA per SM) */
   J2D_OPT_TIMEOUT_MS = 4, /* device-side wait limit in milliseconds (default 2000) */
   J2D_OPT_VERBOSE = 5,    /* 1 = print the chosen configuration to stderr at run time */
-  J2D_OPT_GRAPH = 6       /* 1 = forward runs are captured into a CUDA graph on first use (per
+  J2D_OPT_GRAPH = 6,      /* 1 = forward runs are captured into a CUDA graph on first use (per
                              buffers and step count) and replayed by later identical calls */
+  J2D_OPT_TIMING = 7      /* 1 = runs record CUDA events around their stencil kernels, read
+                             by j2d5pt_kernel_time (ignored for graph replays) */
 } j2d_option;
 
 /* ---- plans ------------------------------------------------------------- */
@@ -183,6 +185,11 @@ j2d_status j2d5pt_autotune(j2d5pt_plan_t plan, const void *in, void *out, long s
  * temporal depth and tile shape of the batched kernel. */
 j2d_status j2d5pt_autotune_batched(j2d5pt_plan_t plan, const void *const *in, void *const *out,
                                    long steps, void *stream);
+
+/* Device time in milliseconds from just before the first to just after the
+ * last stencil kernel of the plan's most recent run (ring copies and other
+ * set-up excluded), with J2D_OPT_TIMING set.  Synchronises on the end event. */
+j2d_status j2d5pt_kernel_time(j2d5pt_plan_t plan, double *ms);
 
 /* Measured fused multiply-add throughput of the current device for `dtype`
  * (FMA instructions per second), from a short dependent-free FMA loop.  Used

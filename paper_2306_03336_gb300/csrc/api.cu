@@ -65,6 +65,10 @@ struct j2d5pt_plan_s {
   DtbState dtb;
   cudaStream_t last_stream = nullptr;
   bool ran = false;
+  // kernel timing events (J2D_OPT_TIMING)
+  int opt_timing = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
   // CUDA graph of the last forward run (J2D_OPT_GRAPH)
   int opt_graph = 0;
   std::vector<const void *> g_in;
@@ -150,6 +154,8 @@ extern "C" j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t p) {
   if (p->ran && p->last_stream) cudaStreamSynchronize(p->last_stream);
   drop_graph(p);
   if (p->g_stream) cudaStreamDestroy(p->g_stream);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
   dtb_release(p->dtb);
   cudaFree(p->ws);
   cudaFree(p->partials);
@@ -212,6 +218,14 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
       p->opt_graph = v != 0;
       drop_graph(p);
       break;
+    case J2D_OPT_TIMING:
+      p->opt_timing = v != 0;
+      if (p->opt_timing && !p->ev0) {
+        cudaEventCreate(&p->ev0);
+        cudaEventCreate(&p->ev1);
+      }
+      drop_graph(p);
+      break;
     default:
       return fail(J2D_ERR_ARG, "set_option: unknown option %d", (int)opt);
   }
@@ -228,6 +242,7 @@ extern "C" j2d_status j2d5pt_get_option(j2d5pt_plan_t p, j2d_option opt, long *v
     case J2D_OPT_TIMEOUT_MS: *v = p->opt_timeout_ms; break;
     case J2D_OPT_VERBOSE: *v = p->opt_verbose; break;
     case J2D_OPT_GRAPH: *v = p->opt_graph; break;
+    case J2D_OPT_TIMING: *v = p->opt_timing; break;
     default: return fail(J2D_ERR_ARG, "get_option: unknown option %d", (int)opt);
   }
   return J2D_OK;
@@ -283,10 +298,16 @@ static j2d_status run_grid_onestep(j2d5pt_plan_t p, int gi, const void *in, void
     if ((e = cudaMemcpyAsync(ws, in, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return cuda_fail(e, "run: copy");
     src = ws;
   }
+  const bool timing = p->opt_timing && p->ev0 && gi == 0;
+  if (timing) cudaEventRecord(p->ev0, s);
   for (long t = 0; t < steps; ++t) {
     void *dst = ((steps - 1 - t) % 2 == 0) ? out : ws;
     if ((e = launch_onestep(p->dtype, adj, src, dst, g, s)) != cudaSuccess) return cuda_fail(e, "run: one-step launch");
     src = dst;
+  }
+  if (p->opt_timing && p->ev1 && gi == (int)p->grids.size() - 1) {
+    cudaEventRecord(p->ev1, s);
+    p->timed = true;
   }
   return J2D_OK;
 }
@@ -329,6 +350,13 @@ static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const
   r.timeout_ns = (unsigned long long)p->opt_timeout_ms * 1000000ull;
   r.sms = p->sms;
   r.smem_optin = p->smem_optin;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (p->opt_timing && p->ev0 && cap == cudaStreamCaptureStatusNone) {
+    r.ev0 = p->ev0;
+    r.ev1 = p->ev1;
+    p->timed = true;
+  }
   std::string err;
   cudaError_t e = dtb_run(p->dtb, r, s, err);
   if (e == cudaErrorNotSupported) return fail(J2D_ERR_UNSUPPORTED, "run: %s", err.c_str());
@@ -580,6 +608,17 @@ extern "C" j2d_status j2d5pt_autotune_batched(j2d5pt_plan_t p, const void *const
   if (!p || !in || !out) return fail(J2D_ERR_ARG, "autotune_batched: null argument");
   if (steps < 1) return fail(J2D_ERR_ARG, "autotune_batched: steps must be >= 1");
   return autotune_common(p, in, out, steps, (cudaStream_t)stream);
+}
+
+extern "C" j2d_status j2d5pt_kernel_time(j2d5pt_plan_t p, double *ms) {
+  if (!p || !ms) return fail(J2D_ERR_ARG, "kernel_time: null argument");
+  if (!p->opt_timing || !p->timed) return fail(J2D_ERR_ARG, "kernel_time: no timed run (set J2D_OPT_TIMING first)");
+  cudaError_t e = cudaEventSynchronize(p->ev1);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel_time: sync");
+  float f = 0;
+  if ((e = cudaEventElapsedTime(&f, p->ev0, p->ev1)) != cudaSuccess) return cuda_fail(e, "kernel_time: elapsed");
+  *ms = f;
+  return J2D_OK;
 }
 
 extern "C" j2d_status j2d5pt_measure_fma_rate(j2d_dtype dt, double *rate) {

@@ -950,8 +950,13 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   cfg.numAttrs = 1;
   void *args[] = {&kp};
   note_launch();
+  if (r.ev0) cudaEventRecord(r.ev0, s);
   e = cudaLaunchKernelExC(&cfg, fn, args);
-  if (e != cudaSuccess) err = "cooperative launch";
+  if (e != cudaSuccess) {
+    err = "cooperative launch";
+    return e;
+  }
+  if (r.ev1) cudaEventRecord(r.ev1, s);
   return e;
 }
 

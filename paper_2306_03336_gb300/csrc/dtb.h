@@ -33,6 +33,7 @@ struct DtbRun {
   unsigned long long timeout_ns = 0;
   int sms = 0;
   size_t smem_optin = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the kernel if set
 };
 
 // Device scratch and cached launch data owned by a plan.

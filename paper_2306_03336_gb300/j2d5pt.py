@@ -20,7 +20,7 @@ J2D_F64, J2D_F32 = 0, 1
 J2D_OK, J2D_ERR_ARG, J2D_ERR_ALIGN, J2D_ERR_NOMEM, J2D_ERR_DEVICE = 0, 1, 2, 3, 4
 J2D_ERR_UNSUPPORTED, J2D_ERR_TIMEOUT, J2D_ERR_BOUNDS = 5, 6, 7
 ALGO = {"auto": 0, "onestep": 1, "resident": 2, "bands": 3, "tiles": 4}
-OPT = {"algo": 0, "depth": 1, "tile_wx": 2, "ctas": 3, "timeout_ms": 4, "verbose": 5, "graph": 6}
+OPT = {"algo": 0, "depth": 1, "tile_wx": 2, "ctas": 3, "timeout_ms": 4, "verbose": 5, "graph": 6, "timing": 7}
 STATUS_NAMES = {0: "J2D_OK", 1: "J2D_ERR_ARG", 2: "J2D_ERR_ALIGN", 3: "J2D_ERR_NOMEM", 4: "J2D_ERR_DEVICE",
                 5: "J2D_ERR_UNSUPPORTED", 6: "J2D_ERR_TIMEOUT", 7: "J2D_ERR_BOUNDS"}
 
@@ -63,6 +63,7 @@ def load():
         "j2d5pt_autotune_batched": [P, P, P, L, P],
         "j2d5pt_measure_fma_rate": [I, ctypes.POINTER(D)],
         "j2d5pt_weight_grad_noalloc": [I, I, I, P, P, P, P],
+        "j2d5pt_kernel_time": [P, ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -203,6 +204,12 @@ def j2d5pt_autotune_batched(h, srcs, dsts, steps, stream=None):
                                           int(steps), _stream_ptr(stream)))
 
 
+def j2d5pt_kernel_time(h):
+    ms = ctypes.c_double()
+    _check(load().j2d5pt_kernel_time(h, ctypes.byref(ms)))
+    return ms.value
+
+
 def j2d5pt_measure_fma_rate(dtype):
     r = ctypes.c_double()
     _check(load().j2d5pt_measure_fma_rate(int(dtype), ctypes.byref(r)))
@@ -283,6 +290,9 @@ class Plan:
 
     def get(self, opt):
         return j2d5pt_get_option(self.handle, opt)
+
+    def kernel_time(self):
+        return j2d5pt_kernel_time(self.handle)
 
     def set_weights(self, weights, i=0):
         j2d5pt_set_weights(self.handle, i, weights)
