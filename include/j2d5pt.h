@@ -78,8 +78,11 @@ typedef enum {
   J2D_OPT_VERBOSE = 5,    /* 1 = print the chosen configuration to stderr at run time */
   J2D_OPT_GRAPH = 6,      /* 1 = forward runs are captured into a CUDA graph on first use (per
                              buffers and step count) and replayed by later identical calls */
-  J2D_OPT_TIMING = 7      /* 1 = runs record CUDA events around their stencil kernels, read
+  J2D_OPT_TIMING = 7,     /* 1 = runs record CUDA events around their stencil kernels, read
                              by j2d5pt_kernel_time (ignored for graph replays) */
+  J2D_OPT_FAULT_INJECT = 8 /* testing: 1 = in the resident and bands kernels, the first strip
+                              never publishes its step counter to other CTAs, so its neighbours'
+                              bounded waits expire and the run reports J2D_ERR_TIMEOUT */
 } j2d_option;
 
 /* ---- plans ------------------------------------------------------------- */

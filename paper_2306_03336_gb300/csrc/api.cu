@@ -51,6 +51,7 @@ struct j2d5pt_plan_s {
   // options
   int opt_algo = J2D_ALGO_AUTO, opt_depth = 0, opt_tile_wx = 0, opt_ctas = 0, opt_verbose = 0;
   int opt_timeout_ms = 2000;
+  int opt_fault = 0;
   // device info
   int sms = 0;
   size_t smem_optin = 0;
@@ -218,6 +219,10 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
       p->opt_graph = v != 0;
       drop_graph(p);
       break;
+    case J2D_OPT_FAULT_INJECT:
+      p->opt_fault = v != 0;
+      drop_graph(p);
+      break;
     case J2D_OPT_TIMING:
       p->opt_timing = v != 0;
       if (p->opt_timing && !p->ev0) {
@@ -243,6 +248,7 @@ extern "C" j2d_status j2d5pt_get_option(j2d5pt_plan_t p, j2d_option opt, long *v
     case J2D_OPT_VERBOSE: *v = p->opt_verbose; break;
     case J2D_OPT_GRAPH: *v = p->opt_graph; break;
     case J2D_OPT_TIMING: *v = p->opt_timing; break;
+    case J2D_OPT_FAULT_INJECT: *v = p->opt_fault; break;
     default: return fail(J2D_ERR_ARG, "get_option: unknown option %d", (int)opt);
   }
   return J2D_OK;
@@ -348,6 +354,7 @@ static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const
   r.cfg = c;
   r.status = p->d_status;
   r.timeout_ns = (unsigned long long)p->opt_timeout_ms * 1000000ull;
+  r.mute_slot = p->opt_fault ? 0 : -1;
   r.sms = p->sms;
   r.smem_optin = p->smem_optin;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

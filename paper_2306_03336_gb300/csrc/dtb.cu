@@ -72,6 +72,7 @@ struct KParams {
   int *gflags;              // per slot step counters (cross-CTA consumers)
   void *gslots;             // per slot mailboxes (cross-CTA consumers)
   unsigned long long timeout_ns;
+  int mute_slot;            // fault injection: this slot never publishes its step counter (-1: none)
 };
 
 // Layout of one warp's shared-memory region (elements of T).
@@ -323,7 +324,7 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
     if (!any_remote) return;
     fence_acq_rel_gpu();
     __syncwarp();
-    if (lane == 0) st_relaxed_gpu(kp.gflags + slot, value);
+    if (lane == 0 && slot != kp.mute_slot) st_relaxed_gpu(kp.gflags + slot, value);
     __syncwarp();
   };
 
@@ -931,6 +932,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   kp.gflags = reinterpret_cast<int *>(sc + 256);
   kp.gslots = sc + 256 + nslots * sizeof(int);
   kp.timeout_ns = r.timeout_ns;
+  kp.mute_slot = r.mute_slot;
 
   const size_t smem = dtb_smem_bytes((int)elem, rmax, rp);
   void *fn = dt == J2D_F64 ? kernel_ptr<double>(mode, r.adjoint) : kernel_ptr<float>(mode, r.adjoint);

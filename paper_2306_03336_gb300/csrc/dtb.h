@@ -34,6 +34,7 @@ struct DtbRun {
   int sms = 0;
   size_t smem_optin = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the kernel if set
+  int mute_slot = -1;                         // fault injection (J2D_OPT_FAULT_INJECT)
 };
 
 // Device scratch and cached launch data owned by a plan.

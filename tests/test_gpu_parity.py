@@ -216,3 +216,24 @@ def test_adjoint_all_kernels(algo, nx, ny):
         assert rel_err(got, ref) <= TOL_F64, (nx, ny, steps)
         one = gpu_run(lam, w, steps, algo="onestep", adjoint=True)
         assert np.all(got == one)  # numerically identical (sign of zero aside)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    # a strip whose step counter is never published (host-set fault injection):
+    # its neighbours' waits run out after the plan's limit, the kernel finishes,
+    # the status says J2D_ERR_TIMEOUT, and the next run on the same plan is correct
+    nx, ny, steps = 2048, 512, 20
+    u0 = synth.field(nx, ny, 91)
+    w = synth.weights(92)
+    p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", "resident").set("timeout_ms", 100).set("fault_inject", 1)
+    src = p.to_device(u0)
+    dst = p.empty()
+    p.run(src, dst, steps)
+    with pytest.raises(j2d5pt.J2DError) as e:
+        p.sync()
+    assert e.value.status == j2d5pt.J2D_ERR_TIMEOUT
+    p.set("fault_inject", 0)
+    p.run(src, dst, steps)
+    p.sync()
+    assert rel_err(p.to_host(dst), oracle.run(u0, w, steps, threads=4)) <= TOL_F64
+    p.close()
