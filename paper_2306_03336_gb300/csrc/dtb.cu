@@ -528,10 +528,14 @@ __device__ Strip band_strip(const KParams &kp, const int *wave, int slot, int SW
   st.active = slot < ncs * m;
   if (!st.active) return st;
   const int j = slot / m, i = slot % m;
+  // rows spread evenly: strip i gets one of the `extra` leftover rows when
+  // floor((i+1)*extra/m) steps up, so every run of consecutive strips (a CTA)
+  // carries the same work to within one row
   const int hb = by1 - by0, bsz = hb / m, extra = hb % m;
+  const int before = (int)((long)i * extra / m), upto = (int)((long)(i + 1) * extra / m);
   st.g = 0;
-  st.rows = bsz + (i < extra ? 1 : 0);
-  st.y0 = by0 + i * bsz + min(i, extra);
+  st.rows = bsz + (upto - before);
+  st.y0 = by0 + i * bsz + before;
   st.x0 = 1 + j * SWc;
   st.active = st.rows > 0;
   const int ylast = st.y0 + st.rows - 1;

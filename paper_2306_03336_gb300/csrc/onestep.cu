@@ -11,6 +11,8 @@
 // Every cell of the logical array, ring included, is produced: ring and
 // outside cells through the identity links (forward) or the transposed ring
 // links (adjoint) of cell_links(), so one kernel serves both directions.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -35,11 +37,17 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
   constexpr int V = VecOf<T>::V;
   using VT = typename VecOf<T>::type;
   const int lane = threadIdx.x;
-  const long pc0 = (((long)blockIdx.x * kWarpsX + threadIdx.y) * 32 + lane) * V;
+  const int H = ny + 2;
+  // persistent: each warp takes work items (one warp-wide column strip x ROWS
+  // rows) in a grid-stride loop; the grid is sized to the resident capacity
+  const long ncs = (pitch + 32 * V - 1) / (32 * V);
+  const long nitems = ncs * ((H + ROWS - 1) / ROWS);
+  const long nwarps = (long)gridDim.x * kWarpsX;
+  for (long it = (long)blockIdx.x * kWarpsX + threadIdx.y; it < nitems; it += nwarps) {
+  const long pc0 = ((it % ncs) * 32 + lane) * V;
   const bool live = pc0 < pitch;
   const int xl0 = (int)(pc0 - off);  // logical x of element 0
-  const int y0 = blockIdx.y * ROWS;
-  const int H = ny + 2;
+  const int y0 = (int)(it / ncs) * ROWS;
 
   T t[ROWS + 2][V];
 #pragma unroll
@@ -94,6 +102,7 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
       }
     }
     if (live) *reinterpret_cast<VT *>(out + (long)y * pitch + pc0) = pack(o, (VT *)nullptr);
+  }
   }
 }
 
@@ -247,11 +256,35 @@ static dim3 onestep_grid(const GridDesc &g, int vec, int rows, int row0) {
 
 std::atomic<long> g_launches{0};
 
+// Grid of the persistent one-step kernel: enough blocks for every work item,
+// at most the number that fit on the device at once.
+template <typename K>
+static dim3 persistent_grid(K kernel, const GridDesc &g, int vec) {
+  static thread_local int cached_dev = -1, cached_sms = 0;
+  static thread_local const void *cached_k = nullptr;
+  static thread_local int cached_blocks = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != cached_dev || (const void *)kernel != cached_k) {
+    cudaDeviceGetAttribute(&cached_sms, cudaDevAttrMultiProcessorCount, dev);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 32 * kWarpsX, 0);
+    cached_blocks = std::max(1, per) * cached_sms;
+    cached_dev = dev;
+    cached_k = (const void *)kernel;
+  }
+  const long ncs = (g.pitch + 32 * vec - 1) / (32 * vec);
+  const long nitems = ncs * ((g.ny + 2 + kOneRows - 1) / kOneRows);
+  const long need = (nitems + kWarpsX - 1) / kWarpsX;
+  return dim3((unsigned)std::max<long>(1, std::min<long>(need, cached_blocks)));
+}
+
 cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, cudaStream_t s) {
   note_launch();
   const dim3 blk(32, kWarpsX);
   if (dt == J2D_F64) {
-    const dim3 grd = onestep_grid(g, 2, kOneRows, 0);
+    const dim3 grd = adj ? persistent_grid(onestep_kernel<double, true, kOneRows>, g, 2)
+                         : persistent_grid(onestep_kernel<double, false, kOneRows>, g, 2);
     auto w = cast_weights<double>(g.w);
     if (adj)
       onestep_kernel<double, true, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
@@ -260,7 +293,8 @@ cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, co
       onestep_kernel<double, false, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
                                                                   (int)g.off, g.nx, g.ny, w);
   } else {
-    const dim3 grd = onestep_grid(g, 4, kOneRows, 0);
+    const dim3 grd = adj ? persistent_grid(onestep_kernel<float, true, kOneRows>, g, 4)
+                         : persistent_grid(onestep_kernel<float, false, kOneRows>, g, 4);
     auto w = cast_weights<float>(g.w);
     if (adj)
       onestep_kernel<float, true, kOneRows><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
