@@ -62,6 +62,7 @@ struct KParams {
   const GridDev *grids;
   const CUtensorMap *maps;  // per grid: load maps of buf[0..2], store maps of buf[0..2]
   const int *jobs;          // BANDS: 5 ints per wave; TILES: 7 ints per tile
+  const int *job_off;       // TILES: CTA b processes jobs [job_off[b], job_off[b+1])
   int njobs;                // waves (BANDS) or tiles (TILES) per round
   int rounds, depth, last_depth, src0;
   int rmax, rp;             // strip rows (max), mailbox column length
@@ -655,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
         grid_barrier(kp, epoch);
       }
     } else {
-      for (int j = blockIdx.x; j < kp.njobs; j += gridDim.x, ++seq) {
+      for (int j = kp.job_off[blockIdx.x]; j < kp.job_off[blockIdx.x + 1]; ++j, ++seq) {
         const Strip st = tile_strip(kp, kp.jobs + 7 * j, warp, blockIdx.x * kWarps, SWc);
         run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
         __syncthreads();
@@ -845,12 +846,51 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
     }
   }
   const int njobs = (int)(jobs.size() / (mode == MODE_BANDS ? 5 : 7));
+  // TILES: give each CTA a contiguous list of jobs, balanced by cost (cells of
+  // the tile's active strips), largest first onto the least-loaded CTA
+  std::vector<int> job_off;
+  if (mode == MODE_TILES) {
+    const int wx = r.cfg.tile_wx, wy = kWarps / wx;
+    std::vector<std::pair<long, int>> cost(njobs);
+    for (int j = 0; j < njobs; ++j) {
+      const int *t = &jobs[7 * (size_t)j];
+      const GridDesc &g = grids[t[0]];
+      long c = 0;
+      for (int b = 0; b < wy; ++b) {
+        const int y0 = t[2] + b * rmax;
+        if (y0 > g.ny) continue;
+        const int rows = std::min(rmax, g.ny + 1 - y0);
+        for (int a = 0; a < wx; ++a)
+          if (t[1] + a * SW <= g.nx) c += (long)rows * SW;
+      }
+      cost[j] = {c, j};
+    }
+    std::stable_sort(cost.begin(), cost.end(), [](const std::pair<long, int> &x, const std::pair<long, int> &y) {
+      return x.first > y.first;
+    });
+    std::vector<long> load(ctas, 0);
+    std::vector<std::vector<int>> lists(ctas);
+    for (const auto &cj : cost) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[b] += cj.first;
+      lists[b].push_back(cj.second);
+    }
+    std::vector<int> reordered;
+    reordered.reserve(jobs.size());
+    job_off.push_back(0);
+    for (int b = 0; b < ctas; ++b) {
+      for (int j : lists[b]) reordered.insert(reordered.end(), &jobs[7 * (size_t)j], &jobs[7 * (size_t)j] + 7);
+      job_off.push_back((int)(reordered.size() / 7));
+    }
+    jobs.swap(reordered);
+  }
 
   // descriptors: grids, tensor maps, jobs
   const size_t ng = grids.size();
   const size_t off_maps = (ng * sizeof(GridDev) + 127) / 128 * 128;
   const size_t off_jobs = off_maps + ng * 6 * sizeof(CUtensorMap);
-  const size_t desc_bytes = off_jobs + jobs.size() * sizeof(int) + 16;
+  const size_t off_joff = off_jobs + (jobs.size() * sizeof(int) + 15) / 16 * 16;
+  const size_t desc_bytes = off_joff + job_off.size() * sizeof(int) + 16;
   std::vector<char> host(desc_bytes, 0);
   GridDev *hg = reinterpret_cast<GridDev *>(host.data());
   CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(host.data() + off_maps);
@@ -875,6 +915,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
     }
   }
   memcpy(host.data() + off_jobs, jobs.data(), jobs.size() * sizeof(int));
+  if (!job_off.empty()) memcpy(host.data() + off_joff, job_off.data(), job_off.size() * sizeof(int));
   cudaError_t e = cudaSuccess;
   ensure(S.desc, S.desc_bytes, desc_bytes, e);
   if (e != cudaSuccess) { err = "descriptor allocation"; return cudaErrorMemoryAllocation; }
@@ -924,6 +965,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   kp.grids = reinterpret_cast<const GridDev *>(S.desc);
   kp.maps = reinterpret_cast<const CUtensorMap *>((char *)S.desc + off_maps);
   kp.jobs = reinterpret_cast<const int *>((char *)S.desc + off_jobs);
+  kp.job_off = reinterpret_cast<const int *>((char *)S.desc + off_joff);
   kp.njobs = njobs;
   kp.rounds = rounds;
   kp.depth = depth;
