@@ -157,6 +157,19 @@ def gcells(cells, ms):
     return cells / (ms * 1e-3) / 1e9
 
 
+def aggregate(total_ms, cells_per_rank, world, device="cuda"):
+    """Whole-job throughput of `world` replicas: the slowest rank's time
+    (MAX all-reduce) against the cell updates of all ranks.  Returns
+    (max_ms, GCells/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, cells_per_rank * world / (total_ms * 1e-3) / 1e9
+
+
 def run_ours(args):
     import torch
     import __graft_entry__
@@ -194,13 +207,8 @@ def run_ours(args):
     total, kern = timed(plan, fn, args.steps, args.warmup, flush, stream)
     clk = clocks.stop()
     plan.sync()
-    total_ms = sum(total)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     cells = nx * ny * steps_t
-    value = cells * args.steps * world / (total_ms * 1e-3) / 1e9
+    total_ms, value = aggregate(sum(total), cells * args.steps, world)
 
     # roofline of the dominant kernel: the FP64 pipe (one multiply and four
     # fused multiply-adds per cell update: 9 flops in 5 FP64 instructions)
@@ -311,6 +319,26 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64):
         p.close()
         torch.cuda.empty_cache()
     out["16384x16384_1000"] = res
+
+    # 2b) the paper's evaluation domain (Figure 2): 8592 x 8328 run, 8192^2 counted
+    #     as the valid domain ("pruned"), FP64 and FP32, 1000 steps, autotuned
+    pd = {}
+    for dt in ("f64", "f32"):
+        nx_, ny_ = 8592, 8328
+        p = j2d5pt.Plan(nx_, ny_, dt, w)
+        uu = synth.field(nx_, ny_, synth.data_seed(1) + 20)
+        a = p.to_device(uu if dt == "f64" else uu.astype(np.float32))
+        b = p.empty()
+        p.autotune(a, b, 1000)
+        p.set("timing", 1)
+        total, kern = timed(p, lambda: p.run(a, b, 1000, stream), 1, 1, flush, stream)
+        t = min(total)
+        pd[dt] = {"gcells_full_domain": round(gcells(nx_ * ny_ * 1000, t), 2),
+                  "gcells_valid_8192sq": round(gcells(8192 * 8192 * 1000, t), 2), "plan": p.describe()}
+        p.close()
+        del a, b
+        torch.cuda.empty_cache()
+    out["paper_domain_8592x8328_1000"] = pd
 
     # 3) 256 batched FP64 grids, sides uniform in [64, 1024], 200 steps, CUDA graph
     cfg = synth.WORKLOADS["j2d5pt_f64_batch256_200"]
