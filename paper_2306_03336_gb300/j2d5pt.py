@@ -318,10 +318,14 @@ class Plan:
         j2d5pt_weight_grad(self.handle, u_t, lam_t1, dw, stream)
         return dw
 
-    def run_host(self, a, steps):
-        """End to end on host arrays: dense (ny+2, nx+2) in, same shape out."""
+    def run_host(self, a, steps, out=None):
+        """End to end on host arrays: dense (ny+2, nx+2) in, same shape out
+        (`out`, if given, e.g. pinned memory for full copy bandwidth)."""
         a = np.ascontiguousarray(a, dtype=self.np_dtype)
-        out = np.empty_like(a)
+        if out is None:
+            out = np.empty_like(a)
+        elif out.shape != a.shape or out.dtype != a.dtype or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous array like the input")
         j2d5pt_run_host(self.handle, a, out, steps)
         return out
 
