@@ -246,7 +246,11 @@ static Weights<T> cast_weights(const double *w) {
   return r;
 }
 
-constexpr int kOneRows = 8;
+constexpr int kOneRows = 8;       // rows per work item, FP64 (FP64-pipe bound)
+#ifndef J2D_ONE_ROWS_F32
+#define J2D_ONE_ROWS_F32 16
+#endif
+constexpr int kOneRowsF32 = J2D_ONE_ROWS_F32;  // FP32 (HBM bound): more rows, fewer halo re-reads
 
 static dim3 onestep_grid(const GridDesc &g, int vec, int rows, int row0) {
   const long cols_per_block = (long)vec * 32 * kWarpsX;
@@ -259,7 +263,7 @@ std::atomic<long> g_launches{0};
 // Grid of the persistent one-step kernel: enough blocks for every work item,
 // at most the number that fit on the device at once.
 template <typename K>
-static dim3 persistent_grid(K kernel, const GridDesc &g, int vec) {
+static dim3 persistent_grid(K kernel, const GridDesc &g, int vec, int rows) {
   static thread_local int cached_dev = -1, cached_sms = 0;
   static thread_local const void *cached_k = nullptr;
   static thread_local int cached_blocks = 0;
@@ -274,7 +278,7 @@ static dim3 persistent_grid(K kernel, const GridDesc &g, int vec) {
     cached_k = (const void *)kernel;
   }
   const long ncs = (g.pitch + 32 * vec - 1) / (32 * vec);
-  const long nitems = ncs * ((g.ny + 2 + kOneRows - 1) / kOneRows);
+  const long nitems = ncs * ((g.ny + 2 + rows - 1) / rows);
   const long need = (nitems + kWarpsX - 1) / kWarpsX;
   return dim3((unsigned)std::max<long>(1, std::min<long>(need, cached_blocks)));
 }
@@ -283,8 +287,8 @@ cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, co
   note_launch();
   const dim3 blk(32, kWarpsX);
   if (dt == J2D_F64) {
-    const dim3 grd = adj ? persistent_grid(onestep_kernel<double, true, kOneRows>, g, 2)
-                         : persistent_grid(onestep_kernel<double, false, kOneRows>, g, 2);
+    const dim3 grd = adj ? persistent_grid(onestep_kernel<double, true, kOneRows>, g, 2, kOneRows)
+                         : persistent_grid(onestep_kernel<double, false, kOneRows>, g, 2, kOneRows);
     auto w = cast_weights<double>(g.w);
     if (adj)
       onestep_kernel<double, true, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
@@ -293,14 +297,14 @@ cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, co
       onestep_kernel<double, false, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
                                                                   (int)g.off, g.nx, g.ny, w);
   } else {
-    const dim3 grd = adj ? persistent_grid(onestep_kernel<float, true, kOneRows>, g, 4)
-                         : persistent_grid(onestep_kernel<float, false, kOneRows>, g, 4);
+    const dim3 grd = adj ? persistent_grid(onestep_kernel<float, true, kOneRowsF32>, g, 4, kOneRowsF32)
+                         : persistent_grid(onestep_kernel<float, false, kOneRowsF32>, g, 4, kOneRowsF32);
     auto w = cast_weights<float>(g.w);
     if (adj)
-      onestep_kernel<float, true, kOneRows><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
+      onestep_kernel<float, true, kOneRowsF32><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
                                                                 (int)g.off, g.nx, g.ny, w);
     else
-      onestep_kernel<float, false, kOneRows><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
+      onestep_kernel<float, false, kOneRowsF32><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
                                                                  (int)g.off, g.nx, g.ny, w);
   }
   return cudaGetLastError();
