@@ -199,6 +199,25 @@ j2d_status j2d5pt_kernel_time(j2d5pt_plan_t plan, double *ms);
  * as the arithmetic roofline. Synchronous. */
 j2d_status j2d5pt_measure_fma_rate(j2d_dtype dtype, double *fma_per_s);
 
+/* Measured throughput of the FP64 integer path alone (cells per second on
+ * the current device; see j2d5pt_arith_info), from a short loop of
+ * independent cell evaluations with register inputs.  With the FMA rate this
+ * gives the arithmetic roofline of the FP64 kernels.  Synchronous. */
+j2d_status j2d5pt_measure_exact_rate(double *cells_per_s);
+
+/* FP64 cell arithmetic (all kernels alike, so results do not depend on the
+ * algorithm, depth or tiling).  A cell (x, y) for which bit
+ * ((y & 3) * 2 + (x & 1)) of *exact_mask is set, and whose five weights and
+ * five input values are positive normal numbers with product exponents
+ * within *exact_guard bits of each other and a normal result, gets the
+ * correctly rounded (nearest-even) value of the exact five-term sum,
+ * computed on the integer pipes.  Every other FP64 cell, and every FP32
+ * cell, gets the FMA chain r = S*in[y-1][x]; r = fma(C, in[y][x], r);
+ * r = fma(W, in[y][x-1], r); r = fma(E, in[y][x+1], r);
+ * r = fma(N, in[y+1][x], r) (the adjoint uses its own link weights in the
+ * same roles).  Either pointer may be NULL.  Never fails. */
+j2d_status j2d5pt_arith_info(unsigned *exact_mask, int *exact_guard);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all plans); a diagnostic for launch accounting. */
 long j2d5pt_kernel_launches(void);

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "dtb.h"
 #include "internal.h"
 
@@ -637,6 +638,19 @@ extern "C" j2d_status j2d5pt_measure_fma_rate(j2d_dtype dt, double *rate) {
   if (!rate || (dt != J2D_F64 && dt != J2D_F32)) return fail(J2D_ERR_ARG, "measure_fma_rate: bad argument");
   cudaError_t e = measure_fma(dt, rate);
   if (e != cudaSuccess) return cuda_fail(e, "measure_fma_rate");
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_measure_exact_rate(double *cells_per_s) {
+  if (!cells_per_s) return fail(J2D_ERR_ARG, "measure_exact_rate: null pointer");
+  cudaError_t e = measure_exact(cells_per_s);
+  if (e != cudaSuccess) return cuda_fail(e, "measure_exact_rate");
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_arith_info(unsigned *exact_mask, int *exact_guard) {
+  if (exact_mask) *exact_mask = kExactMask;
+  if (exact_guard) *exact_guard = kExactGuard;
   return J2D_OK;
 }
 

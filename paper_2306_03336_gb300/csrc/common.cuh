@@ -48,6 +48,122 @@ __device__ __forceinline__ T stencil(const Links<T> &a, T xm, T xp, T ym, T c, T
   return r;
 }
 
+// ---- FP64 cells evaluated on the integer pipes -------------------------------
+// GB300 retires two FP64 FMAs per clock per SM, so an FP64 stencil saturates
+// that pipe while the integer pipes idle.  A fixed subset of FP64 cells is
+// therefore evaluated without the FP64 pipe: the update becomes the correctly
+// rounded (round-to-nearest-even) value of the exact five-term sum, computed in
+// 32/64-bit integer arithmetic.  It is an FP64 result at least as accurate as
+// the FMA chain (one rounding instead of five).  Which cells take this path
+// depends only on the cell's logical coordinates (kExactMask), and the fast
+// path's own fallback to stencil() only on the cell's inputs, so every kernel
+// still produces the same bits for the same cell.
+//
+// Fast path: all five weights and values positive normal, exponent spread of
+// the five products at most kExactGuard bits, normal result; otherwise the
+// cell takes the FMA chain.  Exactness: a product of two 53-bit significands
+// has at most 106 bits; shifted into a 128-bit frame with kExactGuard bits of
+// headroom below, five of them sum without loss (< 5 * 2^124 < 2^127), so the
+// frame holds the exact sum and one rounding gives the correctly rounded value.
+#ifndef J2D_EXACT_MASK
+#define J2D_EXACT_MASK 0x0F
+#endif
+// bit (y & 3) * 2 + (x & 1) set: cell (x, y) takes the integer path
+constexpr unsigned kExactMask = J2D_EXACT_MASK;
+constexpr int kExactGuard = 18;
+
+struct ExactW {
+  uint64_t m[5];  // significands with the implicit bit, order xm, xp, ym, c, yp
+  int e[5];       // biased exponents
+  bool ok;        // all five positive normal
+};
+
+__device__ __forceinline__ ExactW exact_weights(const Links<double> &a) {
+  const double w[5] = {a.xm, a.xp, a.ym, a.c, a.yp};
+  ExactW u;
+  u.ok = true;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const uint64_t b = (uint64_t)__double_as_longlong(w[i]);
+    u.e[i] = (int)(b >> 52);  // includes the sign bit: negative weights fail the range test
+    u.ok &= (unsigned)(u.e[i] - 1) < 2046u;
+    u.m[i] = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  }
+  return u;
+}
+
+// Four-word (128-bit) add with carry: a += b.
+__device__ __forceinline__ void add128(uint32_t (&a)[4], uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
+  asm("add.cc.u32 %0, %0, %4;\n\t"
+      "addc.cc.u32 %1, %1, %5;\n\t"
+      "addc.cc.u32 %2, %2, %6;\n\t"
+      "addc.u32 %3, %3, %7;"
+      : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])
+      : "r"(b0), "r"(b1), "r"(b2), "r"(b3));
+}
+
+// Correctly rounded xm*W + xp*E + ym*S + c*C + yp*N on the fast path; returns
+// false (r untouched) when the fast path does not apply.  Significands are
+// split into 32-bit words (high word 21 bits with the implicit bit); a
+// product is four 32x32->64 multiplies; the frame is four 32-bit words.
+__device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double xp, double ym, double c, double yp,
+                                              double &r) {
+  const double v[5] = {xm, xp, ym, c, yp};
+  uint32_t m0[5], m1[5];
+  int E[5];
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const uint32_t hi = (uint32_t)__double2hiint(v[i]);
+    m0[i] = (uint32_t)__double2loint(v[i]);
+    const int e = (int)(hi >> 20);  // includes the sign bit: negative values fail the range test
+    ok &= (unsigned)(e - 1) < 2046u;
+    m1[i] = (hi & 0xFFFFFu) | 0x100000u;
+    E[i] = e + u.e[i];  // product i = p_i * 2^(E[i] - 2150), p_i in [2^104, 2^106)
+  }
+  const int Em = max(max(max(E[0], E[1]), max(E[2], E[3])), E[4]);
+  uint32_t f[4] = {0u, 0u, 0u, 0u};
+  int sall = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int s = kExactGuard - (Em - E[i]);  // frame position: p_i * 2^s, s <= kExactGuard
+    sall |= s;                               // any s < 0 leaves the fast path
+    const uint32_t b0 = (uint32_t)u.m[i], b1 = (uint32_t)(u.m[i] >> 32);
+    const uint64_t p00 = (uint64_t)m0[i] * b0;
+    const uint64_t p01 = (uint64_t)m0[i] * b1 + (p00 >> 32);
+    const uint64_t p10 = (uint64_t)m1[i] * b0 + (uint32_t)p01;
+    const uint64_t p11 = (uint64_t)m1[i] * b1 + (p01 >> 32) + (p10 >> 32);
+    const uint32_t w0 = (uint32_t)p00, w1 = (uint32_t)p10, w2 = (uint32_t)p11, w3 = (uint32_t)(p11 >> 32);
+    add128(f, w0 << (s & 31), __funnelshift_l(w0, w1, s), __funnelshift_l(w1, w2, s), __funnelshift_l(w2, w3, s));
+  }
+  ok &= sall >= 0;
+  // frame F = f[3]:f[2]:f[1]:f[0] = sum * 2^(2150 + kExactGuard - Em), F in [2^122, 2^127)
+  const int z = __clz((int)f[3]) & 31;  // 1..5 on the fast path
+  const uint32_t g3 = __funnelshift_l(f[2], f[3], z), g2 = __funnelshift_l(f[1], f[2], z);
+  const uint32_t g1 = __funnelshift_l(f[0], f[1], z), g0 = f[0] << z;
+  uint64_t kept = ((uint64_t)g3 << 21) | (g2 >> 11);  // the top 53 bits
+  const uint64_t rb = (g2 >> 10) & 1u;
+  const bool sticky = ((g2 & 0x3FFu) | g1 | g0) != 0u;
+  kept += rb & ((uint64_t)sticky | (kept & 1u));
+  const int carry = (int)(kept >> 53) & 1;  // kept <= 2^53 on the fast path
+  kept >>= carry;
+  const int e = Em - 1000 - kExactGuard - z + carry;  // biased exponent of the result
+  ok &= (unsigned)(e - 1) < 2046u;
+  if (ok) r = __longlong_as_double((long long)(((uint64_t)(e - 1) << 52) + kept));
+  return ok;
+}
+
+// Whether cell (x, y) takes the integer path (logical coordinates).
+__device__ __forceinline__ bool exact_cell(int x, int y) { return (kExactMask >> (((y & 3) << 1) | (x & 1))) & 1u; }
+
+// stencil() or, for the cells exact_cell() selects, the integer path.
+__device__ __forceinline__ double stencil_cell(const Links<double> &a, const ExactW &u, bool exact, double xm,
+                                               double xp, double ym, double c, double yp) {
+  double r;
+  if (exact && u.ok && stencil_exact(u, xm, xp, ym, c, yp, r)) return r;
+  return stencil(a, xm, xp, ym, c, yp);
+}
+
 // Link weights of logical cell (x, y) of an nx*ny grid with a one-cell ring.
 // Forward: interior cells use W, E, S, C, N; ring and outside cells keep their
 // value (identity).  Adjoint (the transpose of one forward step): interior

@@ -38,6 +38,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "dtb.h"
@@ -198,7 +199,8 @@ struct RingAcc {
 // from the warp's mailbox (lane 0 reads the x-1 column, lane 31 the x+1 one).
 template <typename T, bool ADJ, bool DEAD>
 __device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int lane, const Links<T> &a,
-                                           const T *hym, const T *hyp, uint32_t dead, RingAcc<T> &rg) {
+                                           const ExactW &u, int xl, int y0, const T *hym, const T *hyp,
+                                           uint32_t dead, RingAcc<T> &rg) {
   constexpr int V = VecOf<T>::V;
   constexpr int SW = 32 * V;
   T ra[V], rb[V], rc[V];
@@ -220,8 +222,13 @@ __device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int
     if (lane == 31) right = h;
     T o[V];
 #pragma unroll
-    for (int e = 0; e < V; ++e)
-      o[e] = stencil(a, e == 0 ? left : rb[e - 1], e == V - 1 ? right : rb[e + 1], ra[e], rb[e], rc[e]);
+    for (int e = 0; e < V; ++e) {
+      const T xm = e == 0 ? left : rb[e - 1], xp = e == V - 1 ? right : rb[e + 1];
+      if constexpr (std::is_same<T, double>::value)
+        o[e] = stencil_cell(a, u, exact_cell(xl + e, y0 + r), xm, xp, ra[e], rb[e], rc[e]);
+      else
+        o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
+    }
     if constexpr (DEAD) {
 #pragma unroll
       for (int e = 0; e < V; ++e)
@@ -305,6 +312,8 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
   // base weights W, E, S, C, N and the links of interior cells
   const T W = (T)gd.w[0], E = (T)gd.w[1], S = (T)gd.w[2], C = (T)gd.w[3], N = (T)gd.w[4];
   const Links<T> a = ADJ ? Links<T>{E, W, N, C, S} : Links<T>{W, E, S, C, N};
+  ExactW u{};
+  if constexpr (std::is_same<T, double>::value) u = exact_weights(a);
 
   // where my incoming halos live (per side) and where my outgoing edges go
   bool remote[4], any_remote = false;
@@ -458,9 +467,9 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
       __syncwarp();
       const T *hcol = mbox + L::side_off(hside, rp) + par * rp;
       if (any_dead)
-        sweep_rows<T, ADJ, true>(drow, hcol, rows, lane, a, hym, hyp, dead, rg);
+        sweep_rows<T, ADJ, true>(drow, hcol, rows, lane, a, u, xl, st.y0, hym, hyp, dead, rg);
       else
-        sweep_rows<T, ADJ, false>(drow, hcol, rows, lane, a, hym, hyp, dead, rg);
+        sweep_rows<T, ADJ, false>(drow, hcol, rows, lane, a, u, xl, st.y0, hym, hyp, dead, rg);
       __syncwarp();
       publish_edges(par ^ 1);
       publish_remote(base + t + 1);

@@ -49,5 +49,6 @@ long wgrad_partial_count(j2d_dtype dt, const GridDesc &g);
 cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,
                          const GridDesc &g, cudaStream_t s);
 cudaError_t measure_fma(j2d_dtype dt, double *rate);
+cudaError_t measure_exact(double *rate);
 
 }  // namespace j2d

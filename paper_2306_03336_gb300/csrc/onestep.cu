@@ -12,6 +12,8 @@
 // outside cells through the identity links (forward) or the transposed ring
 // links (adjoint) of cell_links(), so one kernel serves both directions.
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -71,8 +73,12 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
   }
 
   Links<T> cw[V];  // links of this thread's columns on rows away from the ring
+  ExactW cu[V];    // the same links unpacked for the integer path (FP64)
 #pragma unroll
-  for (int v = 0; v < V; ++v) cw[v] = cell_links<T, ADJ>(xl0 + v, ADJ ? 2 : 1, nx, ny, w);
+  for (int v = 0; v < V; ++v) {
+    cw[v] = cell_links<T, ADJ>(xl0 + v, ADJ ? 2 : 1, nx, ny, w);
+    if constexpr (std::is_same<T, double>::value) cu[v] = exact_weights(cw[v]);
+  }
 
   const bool lval = live && (xl0 - 1 >= 0) && (xl0 - 1 <= nx + 1);
   const bool rval = live && (xl0 + V <= nx + 1);
@@ -91,7 +97,10 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
       for (int v = 0; v < V; ++v) {
         const T xm = v == 0 ? left : t[r + 1][v - 1];
         const T xp = v == V - 1 ? right : t[r + 1][v + 1];
-        o[v] = stencil(cw[v], xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
+        if constexpr (std::is_same<T, double>::value)
+          o[v] = stencil_cell(cw[v], cu[v], exact_cell(xl0 + v, y), xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
+        else
+          o[v] = stencil(cw[v], xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
       }
     } else {
 #pragma unroll
@@ -237,6 +246,31 @@ __global__ void fma_rate_kernel(T *out, int iters, T a, T b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = r0 + r1 + r2 + r3 + r4 + r5 + r6 + r7;
 }
 
+// Integer-path throughput probe: four independent cell evaluations per
+// iteration, each on its own five inputs (a sliding window of its previous
+// outputs), so nothing is hoisted out of the loop.  Weights sum to about 1
+// and the inputs stay in (0, 1): every evaluation takes the fast path.
+__global__ void exact_rate_kernel(double *out, int iters, ExactW u, Links<double> a) {
+  double s[4][5];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) s[j][i] = 0.05 + 0.04 * (j * 5 + i) + threadIdx.x * 1e-6;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const double o = stencil_cell(a, u, true, s[j][0], s[j][1], s[j][2], s[j][3], s[j][4]);
+#pragma unroll
+      for (int i = 4; i > 0; --i) s[j][i] = s[j][i - 1];
+      s[j][0] = o;
+    }
+  }
+  double acc = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc += s[j][0];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 // ---- host launchers --------------------------------------------------------
 
 template <typename T>
@@ -375,6 +409,46 @@ cudaError_t measure_fma(j2d_dtype dt, double *rate) {
   cudaFree(buf);
   if (e != cudaSuccess) return e;
   *rate = (double)grid * blk * iters * 64 / (best * 1e-3);
+  return cudaSuccess;
+}
+
+cudaError_t measure_exact(double *rate) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int blk = 256, grid = sms * 8, iters = 200;
+  void *buf = nullptr;
+  if ((e = cudaMalloc(&buf, sizeof(double) * grid * blk)) != cudaSuccess) return e;
+  const Links<double> a{0.21, 0.19, 0.2, 0.18, 0.22};
+  ExactW u;
+  const double w[5] = {a.xm, a.xp, a.ym, a.c, a.yp};
+  u.ok = true;
+  for (int i = 0; i < 5; ++i) {
+    uint64_t b;
+    memcpy(&b, &w[i], 8);
+    u.e[i] = (int)(b >> 52);
+    u.m[i] = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    exact_rate_kernel<<<grid, blk>>>((double *)buf, iters, u, a);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return e;
+  *rate = (double)grid * blk * iters * 4 / (best * 1e-3);
   return cudaSuccess;
 }
 

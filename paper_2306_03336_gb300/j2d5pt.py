@@ -64,6 +64,8 @@ def load():
         "j2d5pt_measure_fma_rate": [I, ctypes.POINTER(D)],
         "j2d5pt_weight_grad_noalloc": [I, I, I, P, P, P, P],
         "j2d5pt_kernel_time": [P, ctypes.POINTER(D)],
+        "j2d5pt_measure_exact_rate": [ctypes.POINTER(D)],
+        "j2d5pt_arith_info": [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -214,6 +216,19 @@ def j2d5pt_measure_fma_rate(dtype):
     r = ctypes.c_double()
     _check(load().j2d5pt_measure_fma_rate(int(dtype), ctypes.byref(r)))
     return r.value
+
+
+def j2d5pt_measure_exact_rate():
+    r = ctypes.c_double()
+    _check(load().j2d5pt_measure_exact_rate(ctypes.byref(r)))
+    return r.value
+
+
+def j2d5pt_arith_info():
+    """(exact_mask, exact_guard): which FP64 cells take the integer path."""
+    m, g = ctypes.c_uint(), ctypes.c_int()
+    _check(load().j2d5pt_arith_info(ctypes.byref(m), ctypes.byref(g)))
+    return int(m.value), int(g.value)
 
 
 _DT = {"f64": J2D_F64, "f32": J2D_F32, np.float64: J2D_F64, np.float32: J2D_F32}
