@@ -207,7 +207,10 @@ __device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int
 #pragma unroll
   for (int e = 0; e < V; ++e) ra[e] = hym[e];
   vload(drow, false, rb);
-#pragma unroll 2
+  // FP32: unrolling by the window's period (3) lets the compiler rename the
+  // three row registers instead of moving them (measured +9%); FP64 prefers 2
+  constexpr int kUnroll = sizeof(T) == 4 ? 3 : 2;
+#pragma unroll kUnroll
   for (int r = 0; r < rows; ++r) {
     if (r + 1 < rows) {
       vload(drow + (r + 1) * SW, false, rc);
