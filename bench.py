@@ -306,6 +306,12 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
         run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)
         fam[algo] = {"gcells": run, "kernel_gcells": kern, "frac_alu": round(kern / alu64, 3)}
         p.close()
+    # the same resident kernel with every cell on the FMA chain (integer path off)
+    p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", "resident").set("timing", 1).set("int_path", 0)
+    run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)
+    fam["resident_fma_chain_only"] = {"gcells": run, "kernel_gcells": kern,
+                                      "frac_fp64_pipe": round(kern / (fma64 / 5 / 1e9), 3)}
+    p.close()
     out["f64_2048x1536_1000"] = fam
 
     # 2) 16384^2, FP64 and FP32 from the same seeded data, 1000 steps

@@ -80,9 +80,12 @@ typedef enum {
                              buffers and step count) and replayed by later identical calls */
   J2D_OPT_TIMING = 7,     /* 1 = runs record CUDA events around their stencil kernels, read
                              by j2d5pt_kernel_time (ignored for graph replays) */
-  J2D_OPT_FAULT_INJECT = 8 /* testing: 1 = in the resident and bands kernels, the first strip
-                              never publishes its step counter to other CTAs, so its neighbours'
-                              bounded waits expire and the run reports J2D_ERR_TIMEOUT */
+  J2D_OPT_FAULT_INJECT = 8, /* testing: 1 = in the resident and bands kernels, the first strip
+                               never publishes its step counter to other CTAs, so its neighbours'
+                               bounded waits expire and the run reports J2D_ERR_TIMEOUT */
+  J2D_OPT_INT_PATH = 9      /* FP64: 1 (default) = the cells j2d5pt_arith_info selects are
+                               evaluated on the integer pipes; 0 = every cell takes the FMA
+                               chain on the FP64 pipe.  Ignored for FP32. */
 } j2d_option;
 
 /* ---- plans ------------------------------------------------------------- */
@@ -206,8 +209,9 @@ j2d_status j2d5pt_measure_fma_rate(j2d_dtype dtype, double *fma_per_s);
 j2d_status j2d5pt_measure_exact_rate(double *cells_per_s);
 
 /* FP64 cell arithmetic (all kernels alike, so results do not depend on the
- * algorithm, depth or tiling).  A cell (x, y) for which bit
- * ((y & 3) * 2 + (x & 1)) of *exact_mask is set, and whose five weights and
+ * algorithm, depth or tiling).  With J2D_OPT_INT_PATH = 1 (the default), a
+ * cell (x, y) for which bit ((y & 3) * 2 + (x & 1)) of *exact_mask is set, and
+ * whose five weights and
  * five input values are positive normal numbers with product exponents
  * within *exact_guard bits of each other and a normal result, gets the
  * correctly rounded (nearest-even) value of the exact five-term sum,

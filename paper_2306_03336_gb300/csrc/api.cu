@@ -53,6 +53,7 @@ struct j2d5pt_plan_s {
   int opt_algo = J2D_ALGO_AUTO, opt_depth = 0, opt_tile_wx = 0, opt_ctas = 0, opt_verbose = 0;
   int opt_timeout_ms = 2000;
   int opt_fault = 0;
+  int opt_int_path = 1;  // FP64 cells of the kExactMask pattern on the integer pipes
   // device info
   int sms = 0;
   size_t smem_optin = 0;
@@ -79,6 +80,9 @@ struct j2d5pt_plan_s {
   cudaGraphExec_t g_exec = nullptr;
   cudaStream_t g_stream = nullptr;
 };
+
+// Whether a plan's runs put the kExactMask cells on the integer path (FP64 only).
+static int int_path_of(const j2d5pt_plan_s *p) { return p->dtype == J2D_F64 && p->opt_int_path ? 1 : 0; }
 
 static void drop_graph(j2d5pt_plan_t p) {
   if (p->g_exec) cudaGraphExecDestroy(p->g_exec);
@@ -224,6 +228,11 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
       p->opt_fault = v != 0;
       drop_graph(p);
       break;
+    case J2D_OPT_INT_PATH:
+      if (v != 0 && v != 1) return fail(J2D_ERR_ARG, "set_option: int_path must be 0 or 1");
+      p->opt_int_path = (int)v;
+      drop_graph(p);
+      break;
     case J2D_OPT_TIMING:
       p->opt_timing = v != 0;
       if (p->opt_timing && !p->ev0) {
@@ -250,6 +259,7 @@ extern "C" j2d_status j2d5pt_get_option(j2d5pt_plan_t p, j2d_option opt, long *v
     case J2D_OPT_GRAPH: *v = p->opt_graph; break;
     case J2D_OPT_TIMING: *v = p->opt_timing; break;
     case J2D_OPT_FAULT_INJECT: *v = p->opt_fault; break;
+    case J2D_OPT_INT_PATH: *v = p->opt_int_path; break;
     default: return fail(J2D_ERR_ARG, "get_option: unknown option %d", (int)opt);
   }
   return J2D_OK;
@@ -309,7 +319,8 @@ static j2d_status run_grid_onestep(j2d5pt_plan_t p, int gi, const void *in, void
   if (timing) cudaEventRecord(p->ev0, s);
   for (long t = 0; t < steps; ++t) {
     void *dst = ((steps - 1 - t) % 2 == 0) ? out : ws;
-    if ((e = launch_onestep(p->dtype, adj, src, dst, g, s)) != cudaSuccess) return cuda_fail(e, "run: one-step launch");
+    if ((e = launch_onestep(p->dtype, adj, src, dst, g, int_path_of(p), s)) != cudaSuccess)
+      return cuda_fail(e, "run: one-step launch");
     src = dst;
   }
   if (p->opt_timing && p->ev1 && gi == (int)p->grids.size() - 1) {
@@ -356,6 +367,7 @@ static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const
   r.status = p->d_status;
   r.timeout_ns = (unsigned long long)p->opt_timeout_ms * 1000000ull;
   r.mute_slot = p->opt_fault ? 0 : -1;
+  r.int_path = int_path_of(p);
   r.sms = p->sms;
   r.smem_optin = p->smem_optin;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -507,7 +519,7 @@ static std::string tune_key(j2d5pt_plan_t p, long steps) {
     h = (h ^ (unsigned long long)g.nx) * 1099511628211ull;
     h = (h ^ (unsigned long long)g.ny) * 1099511628211ull;
   }
-  k += "|" + std::to_string(p->grids.size()) + "|" + std::to_string(h);
+  k += "|" + std::to_string(p->grids.size()) + "|" + std::to_string(h) + "|ip" + std::to_string(int_path_of(p));
   long b = 1;
   while (b < steps) b <<= 1;
   k += "|" + std::to_string(b);

@@ -55,9 +55,10 @@ __device__ __forceinline__ T stencil(const Links<T> &a, T xm, T xp, T ym, T c, T
 // rounded (round-to-nearest-even) value of the exact five-term sum, computed in
 // 32/64-bit integer arithmetic.  It is an FP64 result at least as accurate as
 // the FMA chain (one rounding instead of five).  Which cells take this path
-// depends only on the cell's logical coordinates (kExactMask), and the fast
-// path's own fallback to stencil() only on the cell's inputs, so every kernel
-// still produces the same bits for the same cell.
+// depends only on the cell's logical coordinates (kExactMask, when the run has
+// the path on), and the fast path's own fallback to
+// stencil() only on the cell's inputs, so every kernel still produces the same
+// bits for the same cell.
 //
 // Fast path: all five weights and values positive normal, exponent spread of
 // the five products at most kExactGuard bits, normal result; otherwise the
@@ -65,11 +66,10 @@ __device__ __forceinline__ T stencil(const Links<T> &a, T xm, T xp, T ym, T c, T
 // has at most 106 bits; shifted into a 128-bit frame with kExactGuard bits of
 // headroom below, five of them sum without loss (< 5 * 2^124 < 2^127), so the
 // frame holds the exact sum and one rounding gives the correctly rounded value.
-#ifndef J2D_EXACT_MASK
-#define J2D_EXACT_MASK 0x0F
-#endif
-// bit (y & 3) * 2 + (x & 1) set: cell (x, y) takes the integer path
-constexpr unsigned kExactMask = J2D_EXACT_MASK;
+// bit (y & 3) * 2 + (x & 1) set: cell (x, y) takes the integer path.  Rows
+// with y mod 4 in {0, 1}: half of the cells, the pattern that measured fastest
+// across the resident, tiles and one-step kernels.
+constexpr unsigned kExactMask = 0x0F;
 constexpr int kExactGuard = 18;
 
 struct ExactW {
@@ -153,8 +153,12 @@ __device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double
   return ok;
 }
 
-// Whether cell (x, y) takes the integer path (logical coordinates).
-__device__ __forceinline__ bool exact_cell(int x, int y) { return (kExactMask >> (((y & 3) << 1) | (x & 1))) & 1u; }
+// Whether cell (x, y) takes the integer path (logical coordinates) in a run
+// with the path on.  The pattern is a compile-time constant, so this reduces
+// to a test of y.
+__device__ __forceinline__ bool exact_cell(int x, int y, bool on) {
+  return on && ((kExactMask >> (((y & 3) << 1) | (x & 1))) & 1u);
+}
 
 // stencil() or, for the cells exact_cell() selects, the integer path.
 __device__ __forceinline__ double stencil_cell(const Links<double> &a, const ExactW &u, bool exact, double xm,

@@ -75,6 +75,7 @@ struct KParams {
   void *gslots;             // per slot mailboxes (cross-CTA consumers)
   unsigned long long timeout_ns;
   int mute_slot;            // fault injection: this slot never publishes its step counter (-1: none)
+  int int_path;             // FP64: the kExactMask cells on the integer path
 };
 
 // Layout of one warp's shared-memory region (elements of T).
@@ -199,8 +200,8 @@ struct RingAcc {
 // from the warp's mailbox (lane 0 reads the x-1 column, lane 31 the x+1 one).
 template <typename T, bool ADJ, bool DEAD>
 __device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int lane, const Links<T> &a,
-                                           const ExactW &u, int xl, int y0, const T *hym, const T *hyp,
-                                           uint32_t dead, RingAcc<T> &rg) {
+                                           const ExactW &u, bool ipath, int xl, int y0, const T *hym,
+                                           const T *hyp, uint32_t dead, RingAcc<T> &rg) {
   constexpr int V = VecOf<T>::V;
   constexpr int SW = 32 * V;
   T ra[V], rb[V], rc[V];
@@ -228,7 +229,7 @@ __device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int
     for (int e = 0; e < V; ++e) {
       const T xm = e == 0 ? left : rb[e - 1], xp = e == V - 1 ? right : rb[e + 1];
       if constexpr (std::is_same<T, double>::value)
-        o[e] = stencil_cell(a, u, exact_cell(xl + e, y0 + r), xm, xp, ra[e], rb[e], rc[e]);
+        o[e] = stencil_cell(a, u, exact_cell(xl + e, y0 + r, ipath), xm, xp, ra[e], rb[e], rc[e]);
       else
         o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
     }
@@ -470,9 +471,9 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
       __syncwarp();
       const T *hcol = mbox + L::side_off(hside, rp) + par * rp;
       if (any_dead)
-        sweep_rows<T, ADJ, true>(drow, hcol, rows, lane, a, u, xl, st.y0, hym, hyp, dead, rg);
+        sweep_rows<T, ADJ, true>(drow, hcol, rows, lane, a, u, kp.int_path != 0, xl, st.y0, hym, hyp, dead, rg);
       else
-        sweep_rows<T, ADJ, false>(drow, hcol, rows, lane, a, u, xl, st.y0, hym, hyp, dead, rg);
+        sweep_rows<T, ADJ, false>(drow, hcol, rows, lane, a, u, kp.int_path != 0, xl, st.y0, hym, hyp, dead, rg);
       __syncwarp();
       publish_edges(par ^ 1);
       publish_remote(base + t + 1);
@@ -991,6 +992,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   kp.gslots = sc + 256 + nslots * sizeof(int);
   kp.timeout_ns = r.timeout_ns;
   kp.mute_slot = r.mute_slot;
+  kp.int_path = r.int_path;
 
   const size_t smem = dtb_smem_bytes((int)elem, rmax, rp);
   void *fn = dt == J2D_F64 ? kernel_ptr<double>(mode, r.adjoint) : kernel_ptr<float>(mode, r.adjoint);

@@ -43,7 +43,8 @@ j2d_status record_error(j2d_status st, const char *fmt, ...);
 extern std::atomic<long> g_launches;
 inline void note_launch(long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, cudaStream_t s);
+cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, int ipath,
+                           cudaStream_t s);
 cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const GridDesc &g, cudaStream_t s);
 long wgrad_partial_count(j2d_dtype dt, const GridDesc &g);
 cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,

@@ -35,7 +35,7 @@ __device__ __forceinline__ float4 pack(const float *o, float4 *) { return make_f
 
 template <typename T, bool ADJ, int ROWS>
 __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, T *__restrict__ out, long pitch,
-                                                      int off, int nx, int ny, Weights<T> w) {
+                                                      int off, int nx, int ny, Weights<T> w, int ipath) {
   constexpr int V = VecOf<T>::V;
   using VT = typename VecOf<T>::type;
   const int lane = threadIdx.x;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
         const T xm = v == 0 ? left : t[r + 1][v - 1];
         const T xp = v == V - 1 ? right : t[r + 1][v + 1];
         if constexpr (std::is_same<T, double>::value)
-          o[v] = stencil_cell(cw[v], cu[v], exact_cell(xl0 + v, y), xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
+          o[v] = stencil_cell(cw[v], cu[v], exact_cell(xl0 + v, y, ipath != 0), xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
         else
           o[v] = stencil(cw[v], xm, xp, t[r][v], t[r + 1][v], t[r + 2][v]);
       }
@@ -317,7 +317,8 @@ static dim3 persistent_grid(K kernel, const GridDesc &g, int vec, int rows) {
   return dim3((unsigned)std::max<long>(1, std::min<long>(need, cached_blocks)));
 }
 
-cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, cudaStream_t s) {
+cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, int ipath,
+                           cudaStream_t s) {
   note_launch();
   const dim3 blk(32, kWarpsX);
   if (dt == J2D_F64) {
@@ -326,20 +327,20 @@ cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, co
     auto w = cast_weights<double>(g.w);
     if (adj)
       onestep_kernel<double, true, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
-                                                                 (int)g.off, g.nx, g.ny, w);
+                                                                 (int)g.off, g.nx, g.ny, w, ipath);
     else
       onestep_kernel<double, false, kOneRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
-                                                                  (int)g.off, g.nx, g.ny, w);
+                                                                  (int)g.off, g.nx, g.ny, w, ipath);
   } else {
     const dim3 grd = adj ? persistent_grid(onestep_kernel<float, true, kOneRowsF32>, g, 4, kOneRowsF32)
                          : persistent_grid(onestep_kernel<float, false, kOneRowsF32>, g, 4, kOneRowsF32);
     auto w = cast_weights<float>(g.w);
     if (adj)
       onestep_kernel<float, true, kOneRowsF32><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
-                                                                (int)g.off, g.nx, g.ny, w);
+                                                                (int)g.off, g.nx, g.ny, w, 0);
     else
       onestep_kernel<float, false, kOneRowsF32><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
-                                                                 (int)g.off, g.nx, g.ny, w);
+                                                                 (int)g.off, g.nx, g.ny, w, 0);
   }
   return cudaGetLastError();
 }

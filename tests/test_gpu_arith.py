@@ -102,10 +102,12 @@ def arith():
     return j2d5pt.j2d5pt_arith_info()
 
 
+@pytest.mark.parametrize("int_path", [1, 0])
 @pytest.mark.parametrize("wname", ["seeded", "short", "negative"])
 @pytest.mark.parametrize("fname", ["uniform", "short", "spread", "mixed"])
-def test_cells_bit_exact(arith, fname, wname):
+def test_cells_bit_exact(arith, fname, wname, int_path):
     mask, guard = arith
+    mask = mask if int_path else 0
     u0 = _fields(NX, NY)[fname]
     w = _weights()[wname]
     steps = 3
@@ -113,7 +115,8 @@ def test_cells_bit_exact(arith, fname, wname):
     for _ in range(steps):
         ref = model_step(ref, w, mask, guard)
     for algo in ALGOS:
-        plan = j2d5pt.Plan(NX, NY, "f64", w).set("algo", algo)
+        plan = j2d5pt.Plan(NX, NY, "f64", w).set("algo", algo).set("int_path", int_path)
+        assert plan.get("int_path") == int_path
         if algo != "onestep":
             plan.set("depth", steps)
         src, dst = plan.to_device(u0), plan.empty()
@@ -122,8 +125,8 @@ def test_cells_bit_exact(arith, fname, wname):
         got = plan.to_host(dst)
         plan.close()
         bad = np.argwhere(got != ref)
-        assert bad.size == 0, "%s/%s/%s: %d cells differ, first (y, x) = %s: %r vs model %r" % (
-            algo, fname, wname, len(bad), tuple(bad[0]), got[tuple(bad[0])], ref[tuple(bad[0])])
+        assert bad.size == 0, "%s/%s/%s/int_path=%d: %d cells differ, first (y, x) = %s: %r vs model %r" % (
+            algo, fname, wname, int_path, len(bad), tuple(bad[0]), got[tuple(bad[0])], ref[tuple(bad[0])])
 
 
 def test_adjoint_interior_bit_exact(arith):
