@@ -2,9 +2,11 @@
 //
 // The stencil (Zhang et al., GPGPU'23, Section 3.1, Listing 1) updates a cell
 // from its x-1, x+1, y-1, centre and y+1 neighbours with weights W, E, S, C, N.
-// Every kernel here evaluates it with the same chain of one product and four
-// fused multiply-adds (stencil() below), so the one-step kernel and the
-// temporally blocked kernels give bit-identical results for the same inputs.
+// Every kernel here evaluates a cell the same way: the chain of one product
+// and four fused multiply-adds (stencil() below) or, for the FP64 cells the
+// integer path selects, the correctly rounded exact sum (stencil_exact()).  So
+// the one-step kernel and the temporally blocked kernels give bit-identical
+// results for the same inputs.
 #pragma once
 
 #include <cstdint>
