@@ -306,6 +306,12 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
         run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)
         fam[algo] = {"gcells": run, "kernel_gcells": kern, "frac_alu": round(kern / alu64, 3)}
         p.close()
+    # the one-step baseline with its 1000 launches replayed from a CUDA graph
+    p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", "onestep").set("timing", 1).set("graph", 1)
+    p.run(src, dst, T, stream)
+    run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)
+    fam["onestep_graph"] = {"gcells": run, "frac_alu": round(run / alu64, 3)}
+    p.close()
     # the same resident kernel with every cell on the FMA chain (integer path off)
     p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", "resident").set("timing", 1).set("int_path", 0)
     run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)

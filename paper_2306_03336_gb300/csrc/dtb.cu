@@ -722,14 +722,13 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   if (algo == J2D_ALGO_AUTO) {
     if (rq.steps < 4) algo = J2D_ALGO_ONESTEP;
     else if (fits) algo = J2D_ALGO_RESIDENT;
-    else if (dt == J2D_F32 || !single) algo = J2D_ALGO_TILES;
-    else algo = J2D_ALGO_ONESTEP;
+    else algo = J2D_ALGO_TILES;
   }
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
   if (algo == J2D_ALGO_BANDS && !single) algo = J2D_ALGO_TILES;
   c.algo = algo;
   c.depth = rq.depth > 0 ? rq.depth : (dt == J2D_F64 ? 4 : 8);
-  c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : 2;
+  c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : (dt == J2D_F64 ? 4 : 2);
   if (algo == J2D_ALGO_RESIDENT) c.depth = (int)std::max<long>(rq.steps, 1);
   return c;
 }

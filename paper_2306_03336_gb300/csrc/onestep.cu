@@ -149,34 +149,35 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const T *__restrict__ u, con
   const bool live = pc0 < pitch;
   const int xl0 = (int)(pc0 - off);
   const int y0 = 1 + blockIdx.y * ROWS;  // interior rows only
-  T t[ROWS + 2][V];
+  // elements outside the logical array read as zero
+  bool xin[V];
 #pragma unroll
-  for (int r = 0; r < ROWS + 2; ++r) {
-    const int y = y0 - 1 + r;
+  for (int v = 0; v < V; ++v) xin[v] = xl0 + v >= 0 && xl0 + v <= nx + 1;
+  auto load_u = [&](int y, T *o) {
     if (live && y <= ny + 1) {
-      unpack<T, V>(*reinterpret_cast<const VT *>(u + (long)y * pitch + pc0), t[r]);
+      unpack<T, V>(*reinterpret_cast<const VT *>(u + (long)y * pitch + pc0), o);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (!xin[v]) o[v] = T(0);
     } else {
 #pragma unroll
-      for (int v = 0; v < V; ++v) t[r][v] = T(0);
+      for (int v = 0; v < V; ++v) o[v] = T(0);
     }
-  }
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int x = xl0 + v;
-    if (x < 0 || x > nx + 1) {
-#pragma unroll
-      for (int r = 0; r < ROWS + 2; ++r) t[r][v] = T(0);
-    }
-  }
+  };
+  // rows streamed through a three-row window (y-1, y, y+1)
+  T um[V], uc[V], up[V];
+  load_u(y0 - 1, um);
+  load_u(y0, uc);
   const bool lval = live && (xl0 - 1 >= 0) && (xl0 - 1 <= nx + 1);
   const bool rval = live && (xl0 + V <= nx + 1);
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll
+#pragma unroll 4
   for (int r = 0; r < ROWS; ++r) {
     const int y = y0 + r;
     if (y > ny) break;
-    T left = __shfl_up_sync(0xffffffffu, t[r + 1][V - 1], 1);
-    T right = __shfl_down_sync(0xffffffffu, t[r + 1][0], 1);
+    load_u(y + 1, up);
+    T left = __shfl_up_sync(0xffffffffu, uc[V - 1], 1);
+    T right = __shfl_down_sync(0xffffffffu, uc[0], 1);
     if (lane == 0) left = lval ? u[(long)y * pitch + pc0 - 1] : T(0);
     if (lane == 31) right = rval ? u[(long)y * pitch + pc0 + V] : T(0);
     T g[V];
@@ -191,13 +192,18 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const T *__restrict__ u, con
       const int x = xl0 + v;
       if (x < 1 || x > nx) continue;
       const double gv = (double)g[v];
-      const double xm = (double)(v == 0 ? left : t[r + 1][v - 1]);
-      const double xp = (double)(v == V - 1 ? right : t[r + 1][v + 1]);
+      const double xm = (double)(v == 0 ? left : uc[v - 1]);
+      const double xp = (double)(v == V - 1 ? right : uc[v + 1]);
       acc[0] = fma(gv, xm, acc[0]);
       acc[1] = fma(gv, xp, acc[1]);
-      acc[2] = fma(gv, (double)t[r][v], acc[2]);
-      acc[3] = fma(gv, (double)t[r + 1][v], acc[3]);
-      acc[4] = fma(gv, (double)t[r + 2][v], acc[4]);
+      acc[2] = fma(gv, (double)um[v], acc[2]);
+      acc[3] = fma(gv, (double)uc[v], acc[3]);
+      acc[4] = fma(gv, (double)up[v], acc[4]);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      um[v] = uc[v];
+      uc[v] = up[v];
     }
   }
   __shared__ double red[kWarpsX][5];
@@ -285,6 +291,7 @@ constexpr int kOneRows = 8;       // rows per work item, FP64 (FP64-pipe bound)
 #define J2D_ONE_ROWS_F32 16
 #endif
 constexpr int kOneRowsF32 = J2D_ONE_ROWS_F32;  // FP32 (HBM bound): more rows, fewer halo re-reads
+constexpr int kWgradRows = 64;    // rows per thread of the weight gradient (streamed): amortises the reduction
 
 static dim3 onestep_grid(const GridDesc &g, int vec, int rows, int row0) {
   const long cols_per_block = (long)vec * 32 * kWarpsX;
@@ -358,21 +365,21 @@ cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const Grid
 
 long wgrad_partial_count(j2d_dtype dt, const GridDesc &g) {
   GridDesc gi = g;
-  const dim3 grd = onestep_grid(gi, dt == J2D_F64 ? 2 : 4, kOneRows, 2);
+  const dim3 grd = onestep_grid(gi, dt == J2D_F64 ? 2 : 4, kWgradRows, 2);
   return (long)grd.x * grd.y;
 }
 
 cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,
                          const GridDesc &g, cudaStream_t s) {
   const dim3 blk(32, kWarpsX);
-  const dim3 grd = onestep_grid(g, dt == J2D_F64 ? 2 : 4, kOneRows, 2);
+  const dim3 grd = onestep_grid(g, dt == J2D_F64 ? 2 : 4, kWgradRows, 2);
   note_launch(2);
   if (dt == J2D_F64)
-    wgrad_kernel<double, kOneRows><<<grd, blk, 0, s>>>((const double *)u, (const double *)lam, g.pitch, (int)g.off,
-                                                       g.nx, g.ny, partials);
+    wgrad_kernel<double, kWgradRows><<<grd, blk, 0, s>>>((const double *)u, (const double *)lam, g.pitch,
+                                                         (int)g.off, g.nx, g.ny, partials);
   else
-    wgrad_kernel<float, kOneRows><<<grd, blk, 0, s>>>((const float *)u, (const float *)lam, g.pitch, (int)g.off,
-                                                      g.nx, g.ny, partials);
+    wgrad_kernel<float, kWgradRows><<<grd, blk, 0, s>>>((const float *)u, (const float *)lam, g.pitch, (int)g.off,
+                                                        g.nx, g.ny, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   wgrad_final_kernel<<<1, 256, 0, s>>>(partials, (long)grd.x * grd.y, dw);
