@@ -165,7 +165,7 @@ j2d_status j2d5pt_weight_grad(j2d5pt_plan_t plan, const void *u_t, const void *l
  * which every GPU that loads the library holds until the process exits.
  * u_t and lam_t1 are nx*ny grids in the plan layout j2d5pt_plan would give for
  * (nx, ny, dtype); dw as for j2d5pt_weight_grad (accumulated).  Grids needing
- * more than 65536 partial-sum blocks (about 2.1e9 FP64 or 4.3e9 FP32 cells)
+ * more than 65536 partial-sum blocks (about 1.1e9 FP64 or 2.1e9 FP32 cells)
  * are rejected with J2D_ERR_ARG.  The first call on each device looks up the
  * array's device address (once, with that device current); make it before
  * any stream capture.  All calls share the one array: calls that overlap on

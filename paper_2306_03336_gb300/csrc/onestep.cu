@@ -145,10 +145,15 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const T *__restrict__ u, con
   constexpr int V = VecOf<T>::V;
   using VT = typename VecOf<T>::type;
   const int lane = threadIdx.x;
-  const long pc0 = (((long)blockIdx.x * kWarpsX + threadIdx.y) * 32 + lane) * V;
-  const bool live = pc0 < pitch;
+  // one work item per warp: a 32-vector column strip x ROWS interior rows,
+  // numbered across the whole grid so no block covers only padding
+  const long ncs = (pitch + 32 * V - 1) / (32 * V);
+  const long item = (long)blockIdx.x * kWarpsX + threadIdx.y;
+  const long nitems = ncs * ((ny + ROWS - 1) / ROWS);
+  const long pc0 = ((item % ncs) * 32 + lane) * V;
+  const bool live = item < nitems && pc0 < pitch;
   const int xl0 = (int)(pc0 - off);
-  const int y0 = 1 + blockIdx.y * ROWS;  // interior rows only
+  const int y0 = 1 + (int)(item / ncs) * ROWS;  // interior rows only
   // elements outside the logical array read as zero
   bool xin[V];
 #pragma unroll
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const T *__restrict__ u, con
 #pragma unroll 4
   for (int r = 0; r < ROWS; ++r) {
     const int y = y0 + r;
-    if (y > ny) break;
+    if (y > ny || item >= nitems) break;
     load_u(y + 1, up);
     T left = __shfl_up_sync(0xffffffffu, uc[V - 1], 1);
     T right = __shfl_down_sync(0xffffffffu, uc[0], 1);
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const T *__restrict__ u, con
   if (threadIdx.y == 0 && lane < 5) {
     double s = 0.0;
     for (int wi = 0; wi < kWarpsX; ++wi) s += red[wi][lane];
-    partials[((long)blockIdx.y * gridDim.x + blockIdx.x) * 5 + lane] = s;
+    partials[(long)blockIdx.x * 5 + lane] = s;
   }
 }
 
@@ -287,17 +292,8 @@ static Weights<T> cast_weights(const double *w) {
 }
 
 constexpr int kOneRows = 8;       // rows per work item, FP64 (FP64-pipe bound)
-#ifndef J2D_ONE_ROWS_F32
-#define J2D_ONE_ROWS_F32 16
-#endif
-constexpr int kOneRowsF32 = J2D_ONE_ROWS_F32;  // FP32 (HBM bound): more rows, fewer halo re-reads
-constexpr int kWgradRows = 64;    // rows per thread of the weight gradient (streamed): amortises the reduction
-
-static dim3 onestep_grid(const GridDesc &g, int vec, int rows, int row0) {
-  const long cols_per_block = (long)vec * 32 * kWarpsX;
-  return dim3((unsigned)((g.pitch + cols_per_block - 1) / cols_per_block),
-              (unsigned)((g.ny + 2 - row0 + rows - 1) / rows));
-}
+constexpr int kOneRowsF32 = 16;   // FP32 (HBM bound): more rows, fewer halo re-reads
+constexpr int kWgradRows = 32;    // rows per thread of the weight gradient (streamed): amortises the reduction
 
 std::atomic<long> g_launches{0};
 
@@ -364,15 +360,16 @@ cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const Grid
 }
 
 long wgrad_partial_count(j2d_dtype dt, const GridDesc &g) {
-  GridDesc gi = g;
-  const dim3 grd = onestep_grid(gi, dt == J2D_F64 ? 2 : 4, kWgradRows, 2);
-  return (long)grd.x * grd.y;
+  const int V = dt == J2D_F64 ? 2 : 4;
+  const long ncs = (g.pitch + 32 * V - 1) / (32 * V);
+  const long nitems = ncs * ((g.ny + kWgradRows - 1) / kWgradRows);
+  return (nitems + kWarpsX - 1) / kWarpsX;
 }
 
 cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,
                          const GridDesc &g, cudaStream_t s) {
   const dim3 blk(32, kWarpsX);
-  const dim3 grd = onestep_grid(g, dt == J2D_F64 ? 2 : 4, kWgradRows, 2);
+  const dim3 grd((unsigned)wgrad_partial_count(dt, g));
   note_launch(2);
   if (dt == J2D_F64)
     wgrad_kernel<double, kWgradRows><<<grd, blk, 0, s>>>((const double *)u, (const double *)lam, g.pitch,
@@ -382,7 +379,7 @@ cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *d
                                                         g.nx, g.ny, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wgrad_final_kernel<<<1, 256, 0, s>>>(partials, (long)grd.x * grd.y, dw);
+  wgrad_final_kernel<<<1, 256, 0, s>>>(partials, (long)grd.x, dw);
   return cudaGetLastError();
 }
 
