@@ -283,10 +283,12 @@ __device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int
 // every warp of the CTA with the same k (inactive strips only take part in
 // the per-step CTA barrier).  Exchange protocol: the four edge mailboxes of a
 // strip are double-buffered by step parity; in step t a strip reads parity
-// t&1 and writes its new edges into its neighbours' parity (t+1)&1.  One CTA
-// barrier per step orders this for neighbours in the same CTA; a neighbour
-// in another CTA is ordered by its published step counter (release/acquire
-// at GPU scope), waited for only by the strips that border it.
+// t&1 and writes its new edges into its neighbours' parity (t+1)&1.  A
+// neighbour is ordered by its published step counter (release/acquire, at
+// CTA scope in shared memory for FP64 neighbours in the same CTA, at GPU
+// scope for a neighbour in another CTA), waited for only by the strips that
+// border it; for FP32, neighbours in the same CTA are ordered by one CTA
+// barrier per step instead.
 template <typename T, bool ADJ>
 __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int warp, int slot, int src, int dst,
                           int k, int base, uint32_t &mbar_phase) {
@@ -334,6 +336,23 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
                       : remote[s] ? gslots + (size_t)n * slot_elems + L::side_off(opp, rp)
                                   : wbase + (size_t)(n % NW) * region + (size_t)kp.rmax * SW + L::side_off(opp, rp);
   }
+  // Neighbours in the same CTA: FP64 strips use the step-counter protocol of
+  // the cross-CTA links (in shared memory), so a warp waits only for its own
+  // neighbours; FP32 strips, whose steps are short, use one CTA barrier per
+  // step (each measured faster for its type).
+  constexpr bool kLocalFlags = sizeof(T) == 8;
+  int *sflags = reinterpret_cast<int *>(smem + 512);
+  bool local[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) local[s] = act && st.link[s] >= 0 && !remote[s];
+  auto publish_local = [&](int value) {
+    if constexpr (kLocalFlags) {
+      fence_acq_rel_cta();
+      __syncwarp();
+      if (lane == 0) st_relaxed_cta(sflags + warp, value);
+      __syncwarp();
+    }
+  };
   auto publish_remote = [&](int value) {
     if (!any_remote) return;
     fence_acq_rel_gpu();
@@ -443,6 +462,7 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
     __syncwarp();
     // ---- publish state-0 edges into the neighbours' parity-0 mailboxes ----
     publish_edges(0);
+    publish_local(base);
     publish_remote(base);
   }
   __syncthreads();
@@ -457,6 +477,11 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
 #pragma unroll
       for (int s = 0; s < 4; ++s)
         if (remote[s]) wait_flag(kp.gflags + st.link[s], true, base + t, kp);
+      if constexpr (kLocalFlags) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (local[s]) wait_flag(sflags + st.link[s] % NW, false, base + t, kp);
+      }
       // halos of state t: rows into registers; remote columns staged into shared memory
       T hym[V], hyp[V];
       vload(inbox[SIDE_YM] + par * SW + lane * V, remote[SIDE_YM], hym);
@@ -476,9 +501,10 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
         sweep_rows<T, ADJ, false>(drow, hcol, rows, lane, a, u, kp.int_path != 0, xl, st.y0, hym, hyp, dead, rg);
       __syncwarp();
       publish_edges(par ^ 1);
+      publish_local(base + t + 1);
       publish_remote(base + t + 1);
     }
-    __syncthreads();
+    if constexpr (!kLocalFlags) __syncthreads();
   }
   if (!act) return;
 
