@@ -315,7 +315,12 @@ static j2d_status run_grid_onestep(j2d5pt_plan_t p, int gi, const void *in, void
     if ((e = cudaMemcpyAsync(ws, in, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return cuda_fail(e, "run: copy");
     src = ws;
   }
-  const bool timing = p->opt_timing && p->ev0 && gi == 0;
+  // no timing events inside a stream capture (a captured event cannot be
+  // synchronised on later)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  const bool timing = p->opt_timing && p->ev0 && gi == 0 && !capturing;
   if (timing) cudaEventRecord(p->ev0, s);
   for (long t = 0; t < steps; ++t) {
     void *dst = ((steps - 1 - t) % 2 == 0) ? out : ws;
@@ -323,7 +328,7 @@ static j2d_status run_grid_onestep(j2d5pt_plan_t p, int gi, const void *in, void
       return cuda_fail(e, "run: one-step launch");
     src = dst;
   }
-  if (p->opt_timing && p->ev1 && gi == (int)p->grids.size() - 1) {
+  if (p->opt_timing && p->ev1 && !capturing && gi == (int)p->grids.size() - 1) {
     cudaEventRecord(p->ev1, s);
     p->timed = true;
   }

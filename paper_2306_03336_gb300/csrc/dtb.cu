@@ -748,6 +748,9 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   if (algo == J2D_ALGO_AUTO) {
     if (rq.steps < 4) algo = J2D_ALGO_ONESTEP;
     else if (fits) algo = J2D_ALGO_RESIDENT;
+    // the adjoint's tiled kernel carries the ring accumulators and measured
+    // slower than its one-step kernel on grids that do not fit on chip
+    else if (rq.adjoint && single) algo = J2D_ALGO_ONESTEP;
     else algo = J2D_ALGO_TILES;
   }
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;

@@ -105,3 +105,21 @@ def test_single_grid_graph_option():
     p.sync()
     assert rel_err(p.to_host(dst), oracle.run(u0, w2, steps)) <= TOL_F64
     p.close()
+
+
+@pytest.mark.parametrize("algo", ["onestep", "resident", "tiles"])
+def test_graph_with_timing(algo):
+    """Timing events are not recorded inside the graph capture, so a plan
+    with both options runs, replays and reports a kernel time afterwards."""
+    nx, ny, steps = 200, 150, 12
+    u0 = synth.field(nx, ny, 611)
+    w = synth.weights(612)
+    p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", algo).set("graph", 1).set("timing", 1)
+    src = p.to_device(u0)
+    dst = p.empty()
+    for _ in range(3):
+        p.run(src, dst, steps)
+        p.sync()
+        assert p.kernel_time() > 0
+    assert rel_err(p.to_host(dst), oracle.run(u0, w, steps)) <= TOL_F64
+    p.close()
