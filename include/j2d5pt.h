@@ -155,6 +155,16 @@ j2d_status j2d5pt_run_adjoint(j2d5pt_plan_t plan, const void *lam_T, void *lam_0
 j2d_status j2d5pt_weight_grad(j2d5pt_plan_t plan, const void *u_t, const void *lam_t1,
                               double *dw, void *stream);
 
+/* One backward step of the gradient in one pass: lam_t = one adjoint step of
+ * lam_t1 (the same values as j2d5pt_run_adjoint(plan, lam_t1, lam_t, 1)) and
+ * dw += the weight_grad contribution of (u_t, lam_t1) (as j2d5pt_weight_grad,
+ * reduced in another fixed order, so the sums may differ from it in the last
+ * bits).  Single-grid plans; lam_t must not alias lam_t1 or u_t.  Buffers in
+ * the plan layout, 16-byte aligned; dw 5 doubles in device memory.
+ * Asynchronous on `stream`. */
+j2d_status j2d5pt_adjoint_step_wgrad(j2d5pt_plan_t plan, const void *u_t, const void *lam_t1, void *lam_t,
+                                     double *dw, void *stream);
+
 /* Same reduction for callers that cannot allocate device memory; no plan
  * needed.  (The paper has no counterpart: this is a deployment variant.)
  * Callers that cannot call cudaMalloc: code running while a stream is being

@@ -6,7 +6,8 @@ its update, Section 3.1, Listing 1):
 
 - lam_T = dL/du_T;  lam_t = M^T lam_{t+1}  (j2d5pt_run_adjoint);
 - dL/du_0 = lam_0;
-- dL/dw_d = sum_t sum_i lam_{t+1}[i] u_t[nbr_d(i)]  (j2d5pt_weight_grad).
+- dL/dw_d = sum_t sum_i lam_{t+1}[i] u_t[nbr_d(i)]  (j2d5pt_weight_grad; in the
+  backward sweep fused with the adjoint step: j2d5pt_adjoint_step_wgrad).
 
 The map is linear in u for fixed weights, so dL/du_0 needs no forward states
 and is one adjoint run.  The weight gradient needs every u_t: the forward keeps
@@ -100,8 +101,8 @@ class _J2D5PTFn(torch.autograd.Function):
                 for i in range(n - 1):
                     plan.run(states[i], states[i + 1], 1)
                 for t in reversed(range(n)):
-                    plan.weight_grad(states[t], lam, dw)  # lam holds lam_{t+1}
-                    plan.run_adjoint(lam, tmp, 1)
+                    # lam holds lam_{t+1}: one pass gives lam_t and the step's dL/dw
+                    plan.adjoint_step_wgrad(states[t], lam, tmp, dw)
                     lam, tmp = tmp, lam
         else:
             plan.run_adjoint(lam, tmp, steps)

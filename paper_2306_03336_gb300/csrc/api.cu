@@ -61,6 +61,7 @@ struct j2d5pt_plan_s {
   void *ws = nullptr;
   std::vector<size_t> ws_off;
   double *partials = nullptr;
+  long max_partials = 0;  // capacity of `partials` in 5-double blocks
   int *d_status = nullptr;
   // host end-to-end staging (device buffers), allocated on first use
   void *h_in_dev = nullptr, *h_out_dev = nullptr;
@@ -132,6 +133,9 @@ static j2d_status plan_common(j2d5pt_plan_t *out, int count, const int *nx, cons
     long np = wgrad_partial_count(dt, g);
     if (np > max_partials) max_partials = np;
   }
+  // room for a persistent grid of the fused adjoint step (up to 8 blocks per SM)
+  max_partials = std::max<long>(max_partials, 8L * std::max(p->sms, 1));
+  p->max_partials = max_partials;
   if ((e = cudaMalloc(&p->ws, ws_bytes)) != cudaSuccess) { delete p; return fail(J2D_ERR_NOMEM, "plan: workspace of %zu bytes: %s", ws_bytes, cudaGetErrorString(e)); }
   if ((e = cudaMalloc(&p->partials, sizeof(double) * 5 * (size_t)max_partials + 64)) != cudaSuccess ||
       (e = cudaMalloc(&p->d_status, 64)) != cudaSuccess || (e = cudaMemset(p->d_status, 0, 64)) != cudaSuccess) {
@@ -465,6 +469,26 @@ extern "C" j2d_status j2d5pt_weight_grad(j2d5pt_plan_t p, const void *u_t, const
   p->ran = true;
   cudaError_t e = launch_wgrad(p->dtype, u_t, lam_t1, dw, p->partials, p->grids[0], s);
   if (e != cudaSuccess) return cuda_fail(e, "weight_grad: launch");
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d5pt_adjoint_step_wgrad(j2d5pt_plan_t p, const void *u_t, const void *lam_t1, void *lam_t,
+                                               double *dw, void *stream) {
+  if (!p || !u_t || !lam_t1 || !lam_t || !dw) return fail(J2D_ERR_ARG, "adjoint_step_wgrad: null argument");
+  if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "adjoint_step_wgrad: batched plans are forward only");
+  if (lam_t == lam_t1 || lam_t == u_t) return fail(J2D_ERR_ARG, "adjoint_step_wgrad: lam_t aliases an input");
+  if (!aligned16(u_t) || !aligned16(lam_t1) || !aligned16(lam_t))
+    return fail(J2D_ERR_ALIGN, "adjoint_step_wgrad: buffer not 16-byte aligned");
+  if (((uintptr_t)dw & 7u) != 0) return fail(J2D_ERR_ALIGN, "adjoint_step_wgrad: dw not 8-byte aligned");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != p->device) return fail(J2D_ERR_DEVICE, "adjoint_step_wgrad: current device %d differs from the plan's device %d", cur, p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  p->ran = true;
+  cudaError_t e = launch_adjoint_wgrad(p->dtype, u_t, lam_t1, lam_t, dw, p->partials, p->max_partials, p->grids[0],
+                                       int_path_of(p), s);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint_step_wgrad: launch");
   return J2D_OK;
 }
 

@@ -49,6 +49,8 @@ cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const Grid
 long wgrad_partial_count(j2d_dtype dt, const GridDesc &g);
 cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,
                          const GridDesc &g, cudaStream_t s);
+cudaError_t launch_adjoint_wgrad(j2d_dtype dt, const void *u, const void *lam1, void *lam0, double *dw,
+                                 double *partials, long max_partials, const GridDesc &g, int ipath, cudaStream_t s);
 cudaError_t measure_fma(j2d_dtype dt, double *rate);
 cudaError_t measure_exact(double *rate);
 

@@ -33,9 +33,34 @@ __device__ __forceinline__ void unpack<float, 4>(const float4 &v, float *o) {
 __device__ __forceinline__ double2 pack(const double *o, double2 *) { return make_double2(o[0], o[1]); }
 __device__ __forceinline__ float4 pack(const float *o, float4 *) { return make_float4(o[0], o[1], o[2], o[3]); }
 
-template <typename T, bool ADJ, int ROWS>
+// Sum the five per-thread accumulators of a (32 x kWarpsX) block in a fixed
+// order (xor tree within a warp, then warps in order) into partials[block].
+__device__ __forceinline__ void block_partials(const double (&acc)[5], double *partials) {
+  __shared__ double red[kWarpsX][5];
+  const int lane = threadIdx.x;
+#pragma unroll
+  for (int d = 0; d < 5; ++d) {
+    double s = acc[d];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[threadIdx.y][d] = s;
+  }
+  __syncthreads();
+  if (threadIdx.y == 0 && lane < 5) {
+    double s = 0.0;
+    for (int wi = 0; wi < kWarpsX; ++wi) s += red[wi][lane];
+    partials[(long)blockIdx.x * 5 + lane] = s;
+  }
+}
+
+// WG (adjoint only): also accumulate the weight gradient of this step,
+// sum over interior cells of in[i] * u[nbr_d(i)] (in = lam_t+1), into one
+// partial sum per block, reduced in a fixed order.
+template <typename T, bool ADJ, int ROWS, bool WG = false>
 __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, T *__restrict__ out, long pitch,
-                                                      int off, int nx, int ny, Weights<T> w, int ipath) {
+                                                      int off, int nx, int ny, Weights<T> w, int ipath,
+                                                      const T *__restrict__ uw = nullptr,
+                                                      double *__restrict__ partials = nullptr) {
   constexpr int V = VecOf<T>::V;
   using VT = typename VecOf<T>::type;
   const int lane = threadIdx.x;
@@ -45,6 +70,7 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
   const long ncs = (pitch + 32 * V - 1) / (32 * V);
   const long nitems = ncs * ((H + ROWS - 1) / ROWS);
   const long nwarps = (long)gridDim.x * kWarpsX;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (long it = (long)blockIdx.x * kWarpsX + threadIdx.y; it < nitems; it += nwarps) {
   const long pc0 = ((it % ncs) * 32 + lane) * V;
   const bool live = pc0 < pitch;
@@ -62,13 +88,29 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
       for (int v = 0; v < V; ++v) t[r][v] = T(0);
     }
   }
+  T uu[WG ? ROWS + 2 : 1][V];
+  if constexpr (WG) {
+#pragma unroll
+    for (int r = 0; r < ROWS + 2; ++r) {
+      const int y = y0 - 1 + r;
+      if (live && y >= 0 && y < H) {
+        unpack<T, V>(*reinterpret_cast<const VT *>(uw + (long)y * pitch + pc0), uu[r]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) uu[r][v] = T(0);
+      }
+    }
+  }
   // Elements outside the logical array (row padding) read as zero.
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int x = xl0 + v;
     if (x < 0 || x > nx + 1) {
 #pragma unroll
-      for (int r = 0; r < ROWS + 2; ++r) t[r][v] = T(0);
+      for (int r = 0; r < ROWS + 2; ++r) {
+        t[r][v] = T(0);
+        if constexpr (WG) uu[r][v] = T(0);
+      }
     }
   }
 
@@ -111,8 +153,28 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
       }
     }
     if (live) *reinterpret_cast<VT *>(out + (long)y * pitch + pc0) = pack(o, (VT *)nullptr);
+    if constexpr (WG) {
+      T ul = __shfl_up_sync(0xffffffffu, uu[r + 1][V - 1], 1);
+      T ur = __shfl_down_sync(0xffffffffu, uu[r + 1][0], 1);
+      if (lane == 0) ul = lval ? uw[(long)y * pitch + pc0 - 1] : T(0);
+      if (lane == 31) ur = rval ? uw[(long)y * pitch + pc0 + V] : T(0);
+      if (y >= 1 && y <= ny) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int x = xl0 + v;
+          if (x < 1 || x > nx) continue;
+          const double gv = (double)t[r + 1][v];
+          acc[0] = fma(gv, (double)(v == 0 ? ul : uu[r + 1][v - 1]), acc[0]);
+          acc[1] = fma(gv, (double)(v == V - 1 ? ur : uu[r + 1][v + 1]), acc[1]);
+          acc[2] = fma(gv, (double)uu[r][v], acc[2]);
+          acc[3] = fma(gv, (double)uu[r + 1][v], acc[3]);
+          acc[4] = fma(gv, (double)uu[r + 2][v], acc[4]);
+        }
+      }
+    }
   }
   }
+  if constexpr (WG) block_partials(acc, partials);
 }
 
 // Copy the ring (rows 0 and ny+1, columns 0 and nx+1) of `in` to `out`.
@@ -211,20 +273,7 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const T *__restrict__ u, con
       uc[v] = up[v];
     }
   }
-  __shared__ double red[kWarpsX][5];
-#pragma unroll
-  for (int d = 0; d < 5; ++d) {
-    double s = acc[d];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[threadIdx.y][d] = s;
-  }
-  __syncthreads();
-  if (threadIdx.y == 0 && lane < 5) {
-    double s = 0.0;
-    for (int wi = 0; wi < kWarpsX; ++wi) s += red[wi][lane];
-    partials[(long)blockIdx.x * 5 + lane] = s;
-  }
+  block_partials(acc, partials);
 }
 
 // dw[d] += sum of the partials in a fixed order (one block).
@@ -294,6 +343,7 @@ static Weights<T> cast_weights(const double *w) {
 constexpr int kOneRows = 8;       // rows per work item, FP64 (FP64-pipe bound)
 constexpr int kOneRowsF32 = 16;   // FP32 (HBM bound): more rows, fewer halo re-reads
 constexpr int kWgradRows = 32;    // rows per thread of the weight gradient (streamed): amortises the reduction
+constexpr int kOneRowsWG = 4;     // rows per work item of the fused adjoint step + weight gradient (registers)
 
 std::atomic<long> g_launches{0};
 
@@ -380,6 +430,32 @@ cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *d
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   wgrad_final_kernel<<<1, 256, 0, s>>>(partials, (long)grd.x, dw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_wgrad(j2d_dtype dt, const void *u, const void *lam1, void *lam0, double *dw,
+                                 double *partials, long max_partials, const GridDesc &g, int ipath, cudaStream_t s) {
+  note_launch(2);
+  const dim3 blk(32, kWarpsX);
+  if (dt == J2D_F64) {
+    auto k = onestep_kernel<double, true, kOneRowsWG, true>;
+    dim3 grd = persistent_grid(k, g, 2, kOneRowsWG);
+    grd.x = (unsigned)std::max<long>(1, std::min<long>(grd.x, max_partials));
+    k<<<grd, blk, 0, s>>>((const double *)lam1, (double *)lam0, g.pitch, (int)g.off, g.nx, g.ny,
+                          cast_weights<double>(g.w), ipath, (const double *)u, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    wgrad_final_kernel<<<1, 256, 0, s>>>(partials, (long)grd.x, dw);
+  } else {
+    auto k = onestep_kernel<float, true, kOneRowsWG, true>;
+    dim3 grd = persistent_grid(k, g, 4, kOneRowsWG);
+    grd.x = (unsigned)std::max<long>(1, std::min<long>(grd.x, max_partials));
+    k<<<grd, blk, 0, s>>>((const float *)lam1, (float *)lam0, g.pitch, (int)g.off, g.nx, g.ny,
+                          cast_weights<float>(g.w), 0, (const float *)u, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    wgrad_final_kernel<<<1, 256, 0, s>>>(partials, (long)grd.x, dw);
+  }
   return cudaGetLastError();
 }
 

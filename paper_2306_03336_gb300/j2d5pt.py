@@ -59,6 +59,7 @@ def load():
         "j2d5pt_run_host": [P, P, P, L],
         "j2d5pt_run_adjoint": [P, P, P, L, P],
         "j2d5pt_weight_grad": [P, P, P, P, P],
+        "j2d5pt_adjoint_step_wgrad": [P, P, P, P, P, P],
         "j2d5pt_sync_status": [P],
         "j2d5pt_autotune": [P, P, P, L, P],
         "j2d5pt_autotune_batched": [P, P, P, L, P],
@@ -184,6 +185,10 @@ def j2d5pt_run_adjoint(h, lam_T, lam_0, steps, stream=None):
 
 def j2d5pt_weight_grad(h, u_t, lam_t1, dw, stream=None):
     _check(load().j2d5pt_weight_grad(h, _ptr(u_t), _ptr(lam_t1), _ptr(dw), _stream_ptr(stream)))
+
+
+def j2d5pt_adjoint_step_wgrad(h, u_t, lam_t1, lam_t, dw, stream=None):
+    _check(load().j2d5pt_adjoint_step_wgrad(h, _ptr(u_t), _ptr(lam_t1), _ptr(lam_t), _ptr(dw), _stream_ptr(stream)))
 
 
 def j2d5pt_weight_grad_noalloc(nx, ny, dtype, u_t, lam_t1, dw, stream=None):
@@ -333,6 +338,11 @@ class Plan:
     def weight_grad(self, u_t, lam_t1, dw, stream=None):
         j2d5pt_weight_grad(self.handle, u_t, lam_t1, dw, stream)
         return dw
+
+    def adjoint_step_wgrad(self, u_t, lam_t1, lam_t, dw, stream=None):
+        """lam_t = one adjoint step of lam_t1; dw += weight gradient of (u_t, lam_t1)."""
+        j2d5pt_adjoint_step_wgrad(self.handle, u_t, lam_t1, lam_t, dw, stream)
+        return lam_t
 
     def run_host(self, a, steps, out=None):
         """End to end on host arrays: dense (ny+2, nx+2) in, same shape out

@@ -153,6 +153,37 @@ def test_weight_grad_against_oracle(dtype):
     assert torch.equal(dw, dw2)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("nx,ny", [(517, 263), (70, 45), (1, 1), (3, 700)])
+def test_adjoint_step_wgrad_fused(dtype, nx, ny):
+    """One pass: lam_t bit-identical to the one-step adjoint, dw equal to the
+    separate reduction up to summation order and to the oracle within 1e-12."""
+    import torch
+    u = synth.field(nx, ny, 54)
+    lam = synth.field(nx, ny, 55)
+    w = synth.weights(56)
+    npd = np.float64 if dtype == "f64" else np.float32
+    u_, lam_ = u.astype(npd).astype(np.float64), lam.astype(npd).astype(np.float64)
+    p = j2d5pt.Plan(nx, ny, dtype, w)
+    U, L1 = p.to_device(u), p.to_device(lam)
+    L0, L0b = p.empty(), p.empty()
+    dw = torch.full((5,), 0.5, dtype=torch.float64, device="cuda")
+    dw_sep = torch.full((5,), 0.5, dtype=torch.float64, device="cuda")
+    p.adjoint_step_wgrad(U, L1, L0, dw)
+    p.weight_grad(U, L1, dw_sep)
+    p.run_adjoint(L1, L0b, 1)
+    p.sync()
+    assert np.array_equal(p.to_host(L0), p.to_host(L0b))
+    ref = oracle.weight_grad(u_, lam_)
+    got, sep = dw.cpu().numpy() - 0.5, dw_sep.cpu().numpy() - 0.5
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(got - sep).max() <= 1e-13 * np.abs(ref).max()
+    if dtype == "f64":
+        assert rel_err(p.to_host(L0), oracle.adjoint_step(lam, w)) <= TOL_F64
+    with pytest.raises(j2d5pt.J2DError):
+        p.adjoint_step_wgrad(U, L1, L1, dw)  # output aliases an input
+
+
 def test_run_host_end_to_end_matches_device_run():
     nx, ny, steps = 300, 200, 11
     u0 = synth.field(nx, ny, 61)
