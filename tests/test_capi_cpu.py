@@ -64,6 +64,19 @@ def test_argument_errors_before_device(lib):
     assert lib.j2d5pt_sync_status(None) == j2d5pt.J2D_ERR_ARG
     r = ctypes.c_double()
     assert lib.j2d5pt_measure_fma_rate(9, ctypes.byref(r)) == j2d5pt.J2D_ERR_ARG
+    assert lib.j2d5pt_adjoint_step_wgrad(None, None, None, None, None, None) == j2d5pt.J2D_ERR_ARG
+    assert lib.j2d5pt_measure_exact_rate(None) == j2d5pt.J2D_ERR_ARG
+    assert lib.j2d5pt_get_option(None, 9, None) == j2d5pt.J2D_ERR_ARG
+
+
+def test_arith_info_without_gpu(lib):
+    """The FP64 cell-evaluation contract is a property of the library: half of
+    the cells (rows with y mod 4 in {0, 1}) on the integer path, 18 guard bits."""
+    m, g = ctypes.c_uint(), ctypes.c_int()
+    assert lib.j2d5pt_arith_info(ctypes.byref(m), ctypes.byref(g)) == j2d5pt.J2D_OK
+    assert m.value == 0x0F and g.value == 18
+    assert lib.j2d5pt_arith_info(None, None) == j2d5pt.J2D_OK
+    assert j2d5pt.j2d5pt_arith_info() == (0x0F, 18)
 
 
 def test_plan_without_gpu_reports_device_error(lib):
