@@ -16,9 +16,10 @@
 // writes its four edges into double-buffered mailboxes of its neighbours
 // (shared memory when the neighbour is in the same CTA, L2-resident global
 // memory otherwise) and publishes a per-warp step counter; a strip waits only
-// for its own (at most four) neighbours' counters.  This replaces the paper's
-// grid-wide barrier per step with neighbour synchronisation that never stalls
-// unrelated warps.  Strips are loaded with 2D TMA tensor copies and written
+// for its own (at most four) neighbours' counters (FP32 strips of one CTA use
+// one CTA barrier per step instead, faster for their short steps).  This
+// replaces the paper's grid-wide barrier per step with neighbour
+// synchronisation that never stalls unrelated CTAs.  Strips are loaded with 2D TMA tensor copies and written
 // back with per-row TMA tensor stores (the store tensor map ends at the last
 // interior row/column, so the ring and padding are never written).
 //

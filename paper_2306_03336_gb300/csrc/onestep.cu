@@ -340,7 +340,7 @@ static Weights<T> cast_weights(const double *w) {
   return r;
 }
 
-constexpr int kOneRows = 8;       // rows per work item, FP64 (FP64-pipe bound)
+constexpr int kOneRows = 8;       // rows per work item, FP64 (arithmetic bound: FP64 and integer pipes)
 constexpr int kOneRowsF32 = 16;   // FP32 (HBM bound): more rows, fewer halo re-reads
 constexpr int kWgradRows = 32;    // rows per thread of the weight gradient (streamed): amortises the reduction
 constexpr int kOneRowsWG = 4;     // rows per work item of the fused adjoint step + weight gradient (registers)
