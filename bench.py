@@ -293,8 +293,11 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
     except Exception:
         pass
     fma32 = j2d5pt.j2d5pt_measure_fma_rate(j2d5pt.J2D_F32)
+    smem = j2d5pt.j2d5pt_measure_smem_bandwidth() / 1e9  # GB/s
     out["peaks"] = {"fp64_gfma_s": round(fma64 / 1e9, 1), "fp32_gfma_s": round(fma32 / 1e9, 1), "hbm_gbs": hbm,
-                    "fp64_alu_gcells": alu64}
+                    "fp64_alu_gcells": alu64, "smem_gbs": round(smem, 1)}
+    # DTB shared-memory traffic per cell update: one read and one write of the
+    # element (the in-place row sweep); frac_smem = that rate / measured peak
 
     # 1) the headline grid through each kernel family
     nx, ny, T = 2048, 1536, 1000
@@ -305,6 +308,8 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
             p.set("depth", depth)
         run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)
         fam[algo] = {"gcells": run, "kernel_gcells": kern, "frac_alu": round(kern / alu64, 3)}
+        if algo != "onestep":
+            fam[algo]["frac_smem"] = round(kern * 16 / smem, 3)
         p.close()
     # the one-step baseline with its 1000 launches replayed from a CUDA graph
     p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", "onestep").set("graph", 1)
@@ -338,11 +343,13 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
         if dt == "f64":
             ent["onestep_frac_alu"] = round(k1 / alu64, 3)
             ent["best_frac_alu"] = round(k2 / alu64, 3)
+            ent["best_frac_smem"] = round(k2 * 16 / smem, 3)
             ref64 = p.view(b).clone()
         else:
             if hbm:
                 ent["onestep_frac_hbm"] = round(k1 * 8 / hbm, 3)
             ent["best_frac_fp32_pipe"] = round(k2 / (fma32 / 5 / 1e9), 3)
+            ent["best_frac_smem"] = round(k2 * 8 / smem, 3)
             got = p.view(b).double()
             ent["max_rel_err_vs_fp64"] = float(((got - ref64).abs().max() / ref64.abs().max()).item())
             del ref64

@@ -212,6 +212,12 @@ j2d_status j2d5pt_kernel_time(j2d5pt_plan_t plan, double *ms);
  * as the arithmetic roofline. Synchronous. */
 j2d_status j2d5pt_measure_fma_rate(j2d_dtype dtype, double *fma_per_s);
 
+/* Measured shared-memory bandwidth of the current device (bytes per second,
+ * loads plus stores), from 16-byte lane-consecutive accesses (the pattern of
+ * the strip sweeps) on every SM.  The shared-memory roofline of the DTB
+ * kernels.  Synchronous. */
+j2d_status j2d5pt_measure_smem_bandwidth(double *bytes_per_s);
+
 /* Measured throughput of the FP64 integer path alone (cells per second on
  * the current device; see j2d5pt_arith_info), from a short loop of
  * independent cell evaluations with register inputs.  With the FMA rate this

@@ -682,6 +682,13 @@ extern "C" j2d_status j2d5pt_measure_fma_rate(j2d_dtype dt, double *rate) {
   return J2D_OK;
 }
 
+extern "C" j2d_status j2d5pt_measure_smem_bandwidth(double *bytes_per_s) {
+  if (!bytes_per_s) return fail(J2D_ERR_ARG, "measure_smem_bandwidth: null pointer");
+  cudaError_t e = measure_smem(bytes_per_s);
+  if (e != cudaSuccess) return cuda_fail(e, "measure_smem_bandwidth");
+  return J2D_OK;
+}
+
 extern "C" j2d_status j2d5pt_measure_exact_rate(double *cells_per_s) {
   if (!cells_per_s) return fail(J2D_ERR_ARG, "measure_exact_rate: null pointer");
   cudaError_t e = measure_exact(cells_per_s);

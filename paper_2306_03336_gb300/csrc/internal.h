@@ -53,5 +53,6 @@ cudaError_t launch_adjoint_wgrad(j2d_dtype dt, const void *u, const void *lam1, 
                                  double *partials, long max_partials, const GridDesc &g, int ipath, cudaStream_t s);
 cudaError_t measure_fma(j2d_dtype dt, double *rate);
 cudaError_t measure_exact(double *rate);
+cudaError_t measure_smem(double *bytes_per_s);
 
 }  // namespace j2d

@@ -533,4 +533,69 @@ cudaError_t measure_exact(double *rate) {
   return cudaSuccess;
 }
 
+// Shared-memory bandwidth probe: each thread owns 8 16-byte slots of a 64 KB
+// buffer (lane-consecutive, bank-conflict free, the access pattern of the
+// strip sweeps) and per step loads one slot and stores it to another of its
+// own, so threads never share an address.
+__global__ void __launch_bounds__(512) smem_rate_kernel(float *out, int iters) {
+  extern __shared__ float4 sbuf[];  // 8 * blockDim.x float4
+  const int t = threadIdx.x, nb = blockDim.x;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sbuf[t + k * nb] = make_float4((float)(t + k), 0.f, 0.f, 0.f);
+  __syncwarp();
+  // volatile accesses: the compiler may not forward a thread's own stores to
+  // its later loads through registers
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(sbuf);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float4 v;
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                   : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                   : "r"(base + (uint32_t)(t + k * nb) * 16u));
+      acc.x += v.x;
+      asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(base + (uint32_t)(t + ((k + 4) & 7) * nb) * 16u),
+                   "f"(v.y), "f"(v.z), "f"(v.w), "f"(v.x + 1.f)
+                   : "memory");
+    }
+  }
+  out[blockIdx.x * nb + t] = acc.x + acc.y + acc.z + acc.w;
+}
+
+cudaError_t measure_smem(double *bytes_per_s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int blk = 512, grid = sms * 2, iters = 2000;
+  const size_t smem = (size_t)8 * blk * sizeof(float4);  // 64 KB
+  if ((e = cudaFuncSetAttribute(smem_rate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  void *buf = nullptr;
+  if ((e = cudaMalloc(&buf, sizeof(float) * grid * blk)) != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    smem_rate_kernel<<<grid, blk, smem>>>((float *)buf, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return e;
+  // 8 loads and 8 stores of 16 bytes per thread per iteration
+  *bytes_per_s = (double)grid * blk * iters * 8 * 2 * 16 / (best * 1e-3);
+  return cudaSuccess;
+}
+
 }  // namespace j2d

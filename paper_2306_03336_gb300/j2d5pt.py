@@ -67,6 +67,7 @@ def load():
         "j2d5pt_weight_grad_noalloc": [I, I, I, P, P, P, P],
         "j2d5pt_kernel_time": [P, ctypes.POINTER(D)],
         "j2d5pt_measure_exact_rate": [ctypes.POINTER(D)],
+        "j2d5pt_measure_smem_bandwidth": [ctypes.POINTER(D)],
         "j2d5pt_arith_info": [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
@@ -221,6 +222,12 @@ def j2d5pt_kernel_time(h):
 def j2d5pt_measure_fma_rate(dtype):
     r = ctypes.c_double()
     _check(load().j2d5pt_measure_fma_rate(int(dtype), ctypes.byref(r)))
+    return r.value
+
+
+def j2d5pt_measure_smem_bandwidth():
+    r = ctypes.c_double()
+    _check(load().j2d5pt_measure_smem_bandwidth(ctypes.byref(r)))
     return r.value
 
 

@@ -66,6 +66,7 @@ def test_argument_errors_before_device(lib):
     assert lib.j2d5pt_measure_fma_rate(9, ctypes.byref(r)) == j2d5pt.J2D_ERR_ARG
     assert lib.j2d5pt_adjoint_step_wgrad(None, None, None, None, None, None) == j2d5pt.J2D_ERR_ARG
     assert lib.j2d5pt_measure_exact_rate(None) == j2d5pt.J2D_ERR_ARG
+    assert lib.j2d5pt_measure_smem_bandwidth(None) == j2d5pt.J2D_ERR_ARG
     assert lib.j2d5pt_get_option(None, 9, None) == j2d5pt.J2D_ERR_ARG
 
 
