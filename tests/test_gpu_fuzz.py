@@ -1,0 +1,72 @@
+"""Seeded random configurations of every kernel family.
+
+Each case draws a grid size, a step count, a kernel family with its temporal
+depth and tile shape, a dtype and a direction, and requires (1) bit-identical
+results to the one-step kernel of the same plan (every family evaluates every
+cell the same way) and (2) agreement with the oracle: within 1e-12 for FP64,
+within the a-priori FP32 bound against the FP32 oracle.  Configurations a
+family cannot run (a tile too small for the depth, a grid that does not fit
+on chip) must be refused with J2D_ERR_UNSUPPORTED, never run wrongly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_03336_gb300 import j2d5pt, synth
+from tests.gpu_util import TOL_F64, f32_bound, rel_err
+
+pytestmark = pytest.mark.gpu
+
+N_CASES = 160
+
+
+def _case(i):
+    r = np.random.Generator(np.random.PCG64(2306033500 + i))
+    nx = int(r.choice([1, 2, 3, 63, 64, 65, 127, 128, 129, 200, 257, 700]) if r.random() < 0.5 else r.integers(1, 701))
+    ny = int(r.integers(1, 501))
+    return dict(
+        nx=nx, ny=ny,
+        steps=int(r.choice([0, 1, 2, 3, 5, 8, 13, 21, 40])),
+        algo=str(r.choice(["resident", "bands", "tiles"])),
+        depth=int(r.choice([1, 2, 3, 4, 6, 8, 12, 16])),
+        wx=int(r.choice([1, 2, 4, 8, 16])),
+        dtype=str(r.choice(["f64", "f32"])),
+        adjoint=bool(r.random() < 0.3),
+        seed=2306033600 + i,
+    )
+
+
+@pytest.mark.parametrize("i", range(N_CASES))
+def test_random_configuration(i):
+    c = _case(i)
+    nx, ny, steps, dt = c["nx"], c["ny"], c["steps"], c["dtype"]
+    u0 = synth.field(nx, ny, c["seed"])
+    w = synth.weights(c["seed"] + 1)
+    p = j2d5pt.Plan(nx, ny, dt, w)
+    src = p.to_device(u0 if dt == "f64" else u0.astype(np.float32))
+    run = p.run_adjoint if c["adjoint"] else p.run
+    # the one-step kernel of the same plan
+    p.set("algo", "onestep")
+    ref_dev = p.empty()
+    run(src, ref_dev, steps)
+    p.sync()
+    ref = p.to_host(ref_dev)
+    # the family under test
+    p.set("algo", c["algo"]).set("depth", c["depth"]).set("tile_wx", c["wx"])
+    out = p.empty()
+    try:
+        run(src, out, steps)
+        p.sync()
+    except j2d5pt.J2DError as e:
+        assert e.status == j2d5pt.J2D_ERR_UNSUPPORTED, (c, str(e))
+        p.close()
+        pytest.skip("refused: %s" % e)
+    got = p.to_host(out)
+    p.close()
+    assert np.array_equal(got, ref), (c, int(np.count_nonzero(got != ref)))
+    if dt == "f64":
+        ora = oracle.adjoint_run(u0, w, steps) if c["adjoint"] else oracle.run(u0, w, steps)
+        assert rel_err(got, ora) <= TOL_F64, c
+    elif not c["adjoint"]:
+        ora = oracle.run_f32(u0.astype(np.float32).astype(np.float64), w, steps)
+        assert rel_err(got, ora) <= f32_bound(steps), c
