@@ -70,3 +70,40 @@ def test_random_configuration(i):
     elif not c["adjoint"]:
         ora = oracle.run_f32(u0.astype(np.float32).astype(np.float64), w, steps)
         assert rel_err(got, ora) <= f32_bound(steps), c
+
+
+N_BATCHES = 12
+
+
+@pytest.mark.parametrize("i", range(N_BATCHES))
+def test_random_batch(i):
+    """A batch of uneven grids with their own weights, one persistent launch:
+    every grid bit-identical to its own single-grid one-step run."""
+    r = np.random.Generator(np.random.PCG64(2306033800 + i))
+    count = int(r.integers(1, 24))
+    sizes = [(int(r.integers(1, 400)), int(r.integers(1, 300))) for _ in range(count)]
+    dt = str(r.choice(["f64", "f32"]))
+    steps = int(r.choice([1, 4, 9, 17]))
+    depth = int(r.choice([1, 2, 4, 8]))
+    wx = int(r.choice([1, 2, 4]))
+    ws = np.stack([synth.weights(2306033900 + 10 * i + g) for g in range(count)])
+    us = [synth.field(nx, ny, 2306034000 + 10 * i + g) for g, (nx, ny) in enumerate(sizes)]
+    p = j2d5pt.Plan.batch(sizes, dt, ws).set("algo", "tiles").set("depth", depth).set("tile_wx", wx)
+    srcs = [p.to_device(u.astype(p.np_dtype), g) for g, u in enumerate(us)]
+    dsts = [p.empty(g) for g in range(count)]
+    try:
+        p.run_batched(srcs, dsts, steps)
+        p.sync()
+    except j2d5pt.J2DError as e:
+        assert e.status == j2d5pt.J2D_ERR_UNSUPPORTED, str(e)
+        p.close()
+        pytest.skip("refused: %s" % e)
+    outs = [p.to_host(d, g) for g, d in enumerate(dsts)]
+    p.close()
+    for g, (nx, ny) in enumerate(sizes):
+        q = j2d5pt.Plan(nx, ny, dt, ws[g]).set("algo", "onestep")
+        a, b = q.to_device(us[g].astype(q.np_dtype)), q.empty()
+        q.run(a, b, steps)
+        q.sync()
+        assert np.array_equal(outs[g], q.to_host(b)), (i, g, nx, ny, dt, steps, depth, wx)
+        q.close()
