@@ -223,41 +223,6 @@ __device__ __forceinline__ void sweep_row(T (&ra)[VecOf<T>::V], T (&rb)[VecOf<T>
     for (int e = 0; e < V; ++e)
       if (dead & (1u << e)) o[e] = rb[e];
   }
-  if constexpr (ADJ) {
-    // ring cells add their link weight times the old adjacent interior value,
-    // rounded as stencil() rounds a ring cell's chain: the row-0 (y+1 link),
-    // column-0 (x+1 link) and column nx+1 (x-1 link) cells add it in one
-    // fused multiply-add after the centre term; the row ny+1 cell's link
-    // (y-1) is the chain's leading product, rounded before the add
-    if (rg.ring) {
-      if (r == 0 && (rg.ring & (1 << SIDE_YM))) {
-#pragma unroll
-        for (int e = 0; e < V; ++e) rg.ym[e] = fma_rn(rg.S, rb[e], rg.ym[e]);
-      }
-      if (r == rows - 1 && (rg.ring & (1 << SIDE_YP))) {
-#pragma unroll
-        for (int e = 0; e < V; ++e) rg.yp[e] = add_rn(rg.yp[e], mul_rn(rg.N, rb[e]));
-      }
-      if (rg.ring & (1 << SIDE_XM)) {
-        const T c0 = __shfl_sync(0xffffffffu, rb[0], 0);
-        if (lane == (r & 31)) {
-          if (r < 32) rg.xm0 = fma_rn(rg.W, c0, rg.xm0);
-          else rg.xm1 = fma_rn(rg.W, c0, rg.xm1);
-        }
-      }
-      if (rg.ring & (1 << SIDE_XP)) {
-        T ce = rb[0];
-#pragma unroll
-        for (int e = 1; e < V; ++e)
-          if (rg.xp_elem == e) ce = rb[e];
-        const T cx = __shfl_sync(0xffffffffu, ce, rg.xp_lane & 31);
-        if (lane == (r & 31)) {
-          if (r < 32) rg.xp0 = fma_rn(rg.E, cx, rg.xp0);
-          else rg.xp1 = fma_rn(rg.E, cx, rg.xp1);
-        }
-      }
-    }
-  }
   vstore(drow + r * SW, o);
 #pragma unroll
   for (int e = 0; e < V; ++e) { ra[e] = rb[e]; rb[e] = rc[e]; }
@@ -302,6 +267,39 @@ __device__ __forceinline__ void sweep_rows(T *drow, const T *hcol, int rows, int
       }
       sweep_row<T, ADJ, DEAD>(ra, rb, rc, drow, hcol, r, rows, lane, a, u, ipath, xl, y0, dead, rg);
     }
+  }
+}
+
+// Adjoint ring cells of a strip bordering the ring, once per step and before
+// the sweep overwrites the strip: each adds its link weight times the old
+// value of its one interior neighbour, rounded as stencil() rounds a ring
+// cell's chain (the row-0, column-0 and column nx+1 cells add it in one fused
+// multiply-add after the centre term; the row ny+1 cell rounds the product
+// first).  Lane r keeps the column rings of row r (and r+32).
+template <typename T>
+__device__ __forceinline__ void ring_accumulate(RingAcc<T> &rg, const T *data, const T *drow, int rows, int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  if (rg.ring & (1 << SIDE_YM)) {
+    T v[V];
+    vload(drow, false, v);
+#pragma unroll
+    for (int e = 0; e < V; ++e) rg.ym[e] = fma_rn(rg.S, v[e], rg.ym[e]);
+  }
+  if (rg.ring & (1 << SIDE_YP)) {
+    T v[V];
+    vload(drow + (rows - 1) * SW, false, v);
+#pragma unroll
+    for (int e = 0; e < V; ++e) rg.yp[e] = add_rn(rg.yp[e], mul_rn(rg.N, v[e]));
+  }
+  if (rg.ring & (1 << SIDE_XM)) {
+    if (lane < rows) rg.xm0 = fma_rn(rg.W, data[lane * SW], rg.xm0);
+    if (lane + 32 < rows) rg.xm1 = fma_rn(rg.W, data[(lane + 32) * SW], rg.xm1);
+  }
+  if (rg.ring & (1 << SIDE_XP)) {
+    const int c = rg.xp_lane * V + rg.xp_elem;  // strip column of grid column nx
+    if (lane < rows) rg.xp0 = fma_rn(rg.E, data[lane * SW + c], rg.xp0);
+    if (lane + 32 < rows) rg.xp1 = fma_rn(rg.E, data[(lane + 32) * SW + c], rg.xp1);
   }
 }
 
@@ -521,6 +519,9 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
       }
       __syncwarp();
       const T *hcol = mbox + L::side_off(hside, rp) + par * rp;
+      if constexpr (ADJ) {
+        if (rg.ring) ring_accumulate(rg, data, drow, rows, lane);
+      }
       if (any_dead)
         sweep_rows<T, ADJ, true>(drow, hcol, rows, lane, a, u, kp.int_path != 0, xl, st.y0, hym, hyp, dead, rg);
       else
@@ -774,9 +775,6 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   if (algo == J2D_ALGO_AUTO) {
     if (rq.steps < 4) algo = J2D_ALGO_ONESTEP;
     else if (fits) algo = J2D_ALGO_RESIDENT;
-    // the adjoint's tiled kernel carries the ring accumulators and measured
-    // slower than its one-step kernel on grids that do not fit on chip
-    else if (rq.adjoint && single) algo = J2D_ALGO_ONESTEP;
     else algo = J2D_ALGO_TILES;
   }
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
