@@ -83,9 +83,13 @@ typedef enum {
   J2D_OPT_FAULT_INJECT = 8, /* testing: 1 = in the resident and bands kernels, the first strip
                                never publishes its step counter to other CTAs, so its neighbours'
                                bounded waits expire and the run reports J2D_ERR_TIMEOUT */
-  J2D_OPT_INT_PATH = 9      /* FP64: 1 (default) = the cells j2d5pt_arith_info selects are
+  J2D_OPT_INT_PATH = 9,     /* FP64: 1 (default) = the cells j2d5pt_arith_info selects are
                                evaluated on the integer pipes; 0 = every cell takes the FMA
                                chain on the FP64 pipe.  Ignored for FP32. */
+  J2D_OPT_SWEEP_STEPS = 10  /* TILES, FP32 forward: time steps per sweep of a strip, 2 (default:
+                               each exchange of halos carries two steps, the strip reading two
+                               cells deep around it) or 1.  Results are identical either way;
+                               ignored elsewhere. */
 } j2d_option;
 
 /* ---- plans ------------------------------------------------------------- */

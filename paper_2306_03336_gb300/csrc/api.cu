@@ -54,6 +54,7 @@ struct j2d5pt_plan_s {
   int opt_timeout_ms = 2000;
   int opt_fault = 0;
   int opt_int_path = 1;  // FP64 cells of the kExactMask pattern on the integer pipes
+  int opt_sweep_steps = 2;  // FP32 tiles, forward: time steps per shared-memory sweep
   // device info
   int sms = 0;
   size_t smem_optin = 0;
@@ -237,6 +238,11 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
       p->opt_int_path = (int)v;
       drop_graph(p);
       break;
+    case J2D_OPT_SWEEP_STEPS:
+      if (v != 1 && v != 2) return fail(J2D_ERR_ARG, "set_option: sweep_steps must be 1 or 2");
+      p->opt_sweep_steps = (int)v;
+      drop_graph(p);
+      break;
     case J2D_OPT_TIMING:
       p->opt_timing = v != 0;
       if (p->opt_timing && !p->ev0) {
@@ -264,6 +270,7 @@ extern "C" j2d_status j2d5pt_get_option(j2d5pt_plan_t p, j2d_option opt, long *v
     case J2D_OPT_TIMING: *v = p->opt_timing; break;
     case J2D_OPT_FAULT_INJECT: *v = p->opt_fault; break;
     case J2D_OPT_INT_PATH: *v = p->opt_int_path; break;
+    case J2D_OPT_SWEEP_STEPS: *v = p->opt_sweep_steps; break;
     default: return fail(J2D_ERR_ARG, "get_option: unknown option %d", (int)opt);
   }
   return J2D_OK;
@@ -278,6 +285,7 @@ static DtbConfig resolve(j2d5pt_plan_t p, long steps, bool adj) {
   rq.ctas = p->opt_ctas;
   rq.steps = steps;
   rq.adjoint = adj;
+  rq.sweep_steps = p->opt_sweep_steps;
   return dtb_choose(p->dtype, p->grids, p->sms, p->smem_optin, rq);
 }
 
@@ -294,9 +302,9 @@ static const char *algo_name(int a) {
 extern "C" j2d_status j2d5pt_describe(j2d5pt_plan_t p, char *buf, size_t len) {
   if (!p || !buf || len == 0) return fail(J2D_ERR_ARG, "describe: null argument");
   DtbConfig c = resolve(p, 1000, false);
-  snprintf(buf, len, "dtype=%s grids=%zu nx=%d ny=%d pitch=%ld offset=%ld algo=%s depth=%d tile_wx=%d ctas=%d rows=%d sms=%d",
+  snprintf(buf, len, "dtype=%s grids=%zu nx=%d ny=%d pitch=%ld offset=%ld algo=%s depth=%d tile_wx=%d ctas=%d rows=%d sweep=%d sms=%d",
            p->dtype == J2D_F64 ? "f64" : "f32", p->grids.size(), p->grids[0].nx, p->grids[0].ny, p->grids[0].pitch,
-           p->grids[0].off, algo_name(c.algo), c.depth, c.tile_wx, c.ctas, c.rows, p->sms);
+           p->grids[0].off, algo_name(c.algo), c.depth, c.tile_wx, c.ctas, c.rows, c.sweep, p->sms);
   return J2D_OK;
 }
 
@@ -548,7 +556,8 @@ static std::string tune_key(j2d5pt_plan_t p, long steps) {
     h = (h ^ (unsigned long long)g.nx) * 1099511628211ull;
     h = (h ^ (unsigned long long)g.ny) * 1099511628211ull;
   }
-  k += "|" + std::to_string(p->grids.size()) + "|" + std::to_string(h) + "|ip" + std::to_string(int_path_of(p));
+  k += "|" + std::to_string(p->grids.size()) + "|" + std::to_string(h) + "|ip" + std::to_string(int_path_of(p)) +
+       "|sw" + std::to_string(p->opt_sweep_steps);
   long b = 1;
   while (b < steps) b <<= 1;
   k += "|" + std::to_string(b);

@@ -50,7 +50,7 @@ constexpr int kWarps = 16;            // warps (strips) per CTA
 constexpr int kThreads = kWarps * 32;
 enum { SIDE_YM = 0, SIDE_YP = 1, SIDE_XM = 2, SIDE_XP = 3 };
 enum { LINK_CONST = -1, LINK_ZERO = -2 };
-enum { MODE_BANDS = 0, MODE_TILES = 1 };
+enum { MODE_BANDS = 0, MODE_TILES = 1, MODE_TILES_PAIR = 2 };
 
 // Per-grid data the kernel reads from global memory.
 struct GridDev {
@@ -105,6 +105,19 @@ __host__ __device__ inline size_t dtb_smem_bytes(int elem, int rmax, int rp) {
   const int per128 = 128 / elem;
   e = (e + per128 - 1) / per128 * per128;
   return (size_t)kHeaderBytes + (size_t)kWarps * e * elem;
+}
+
+// Two-steps-per-sweep tiles (FP32 forward): a warp's region is its strip and
+// four 32-entry halo columns (columns -1 and SW at step t, then at step t+1),
+// with no mailboxes: neighbours' cells are read in place.
+constexpr int kPairCols = 4 * 32;
+__host__ __device__ inline int pair_region_elems(int elem, int rmax) {
+  const int SW = 32 * (16 / elem);
+  const int per128 = 128 / elem;
+  return (rmax * SW + kPairCols + per128 - 1) / per128 * per128;
+}
+__host__ __device__ inline size_t pair_smem_bytes(int elem, int rmax) {
+  return (size_t)kHeaderBytes + (size_t)kWarps * pair_region_elems(elem, rmax) * elem;
 }
 
 // ---- bounded waits ---------------------------------------------------------
@@ -300,6 +313,67 @@ __device__ __forceinline__ void ring_accumulate(RingAcc<T> &rg, const T *data, c
     const int c = rg.xp_lane * V + rg.xp_elem;  // strip column of grid column nx
     if (lane < rows) rg.xp0 = fma_rn(rg.E, data[lane * SW + c], rg.xp0);
     if (lane + 32 < rows) rg.xp1 = fma_rn(rg.E, data[(lane + 32) * SW + c], rg.xp1);
+  }
+}
+
+// Write back the valid part of a strip: whole rows by TMA tensor stores when
+// the strip's columns are all valid (the store map clips beyond column nx),
+// else element by element; adjoint strips bordering the ring also write their
+// ring accumulators.
+template <typename T, bool ADJ>
+__device__ void strip_store(const Strip &st, const GridDev &gd, const T *data, const CUtensorMap *map_store,
+                            T *dstbuf, int lane, const RingAcc<T> &rg) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  const int nx = gd.nx, ny = gd.ny, rows = st.rows;
+  const long pitch = gd.pitch;
+  const int off = gd.off;
+  const bool full = st.sx0 == 0 && st.sx1 == SW;
+  if (full) {
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      for (int r = st.sy0; r < st.sy1; ++r) tma_store_2d(map_store, off + st.x0, st.y0 + r, data + r * SW);
+      bulk_commit();
+      // a tensor store may rewrite the rest of the 16-byte granule holding
+      // column nx, i.e. the ring cell nx+1: let it land before the adjoint
+      // writes the ring below
+      if (ADJ && (st.ring & (1 << SIDE_XP))) {
+        bulk_wait_all();
+        fence_proxy_async_all();
+      }
+    }
+    __syncwarp();
+  } else {
+    for (int r = st.sy0; r < st.sy1; ++r) {
+      const long rowoff = (long)(st.y0 + r) * pitch + off;
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const int c = lane * V + e;
+        if (c >= st.sx0 && c < st.sx1) dstbuf[rowoff + st.x0 + c] = data[r * SW + c];
+      }
+    }
+  }
+  if (ADJ && st.ring) {
+    // ring cells of the valid region
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int c = lane * V + e, x = st.x0 + c;
+      const bool xin = x >= 1 && x <= nx && c >= st.sx0 && c < st.sx1;
+      if ((st.ring & (1 << SIDE_YM)) && xin && st.sy0 == 0) dstbuf[off + x] = rg.ym[e];
+      if ((st.ring & (1 << SIDE_YP)) && xin && st.sy1 == rows) dstbuf[(long)(ny + 1) * pitch + off + x] = rg.yp[e];
+    }
+    if ((st.ring & (1 << SIDE_XM)) && st.sx0 == 0) {
+      if (lane < rows && lane >= st.sy0 && lane < st.sy1) dstbuf[(long)(st.y0 + lane) * pitch + off] = rg.xm0;
+      if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
+        dstbuf[(long)(st.y0 + lane + 32) * pitch + off] = rg.xm1;
+    }
+    if ((st.ring & (1 << SIDE_XP)) && (nx - st.x0) < st.sx1) {
+      if (lane < rows && lane >= st.sy0 && lane < st.sy1)
+        dstbuf[(long)(st.y0 + lane) * pitch + off + nx + 1] = rg.xp0;
+      if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
+        dstbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1] = rg.xp1;
+    }
   }
 }
 
@@ -535,54 +609,281 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
   }
   if (!act) return;
 
-  // ---- store the valid part ----
-  const bool full = st.sx0 == 0 && st.sx1 == SW;
-  if (full) {
-    fence_proxy_async_smem();
-    __syncwarp();
-    if (lane == 0) {
-      for (int r = st.sy0; r < st.sy1; ++r) tma_store_2d(map_store, off + st.x0, st.y0 + r, data + r * SW);
-      bulk_commit();
-      // a tensor store may rewrite the rest of the 16-byte granule holding
-      // column nx, i.e. the ring cell nx+1: let it land before the adjoint
-      // writes the ring below
-      if (ADJ && (st.ring & (1 << SIDE_XP))) {
-        bulk_wait_all();
-        fence_proxy_async_all();
-      }
-    }
-    __syncwarp();
-  } else {
-    for (int r = st.sy0; r < st.sy1; ++r) {
-      const long rowoff = (long)(st.y0 + r) * pitch + off;
+  strip_store<T, ADJ>(st, gd, data, map_store, dstbuf, lane, rg);
+}
+
+// ---- two time steps per sweep (TILES, FP32 forward) -------------------------
+//
+// An exchange carries two steps.  A strip reads, in place from its neighbours'
+// shared memory, the state-t cells two deep around it (rows -2, -1, R, R+1,
+// columns -2, -1, SW, SW+1) and the four diagonal cells beside its corners,
+// and evaluates step t+1 on the one-cell ring around itself exactly as the
+// strip owning each of those cells does.  After a CTA barrier (every strip
+// has read its neighbours) it sweeps its rows once, computing step t+1 of row
+// r and step t+2 of row r-1 from two register windows, and stores step t+2 in
+// place; a second barrier ends the exchange.  Per two steps: one shared-memory
+// load and store per row, no mailbox copies, two CTA barriers.  Sides without
+// a neighbour (ring, overlapped tile halo) keep the values read at the strip's
+// load, as in the single-step exchange.
+
+// One row of a sweep: new values from the old rows above (ra), at (rb) and
+// below (rc); lane 0 takes x-1 from hl, lane 31 takes x+1 from hr; dead
+// columns keep their value.  The same evaluation as sweep_row().
+template <typename T, bool DEAD>
+__device__ __forceinline__ void row_update(const T (&ra)[VecOf<T>::V], const T (&rb)[VecOf<T>::V],
+                                           const T (&rc)[VecOf<T>::V], T hl, T hr, int lane, const Links<T> &a,
+                                           uint32_t dead, T (&o)[VecOf<T>::V]) {
+  constexpr int V = VecOf<T>::V;
+  T left = __shfl_up_sync(0xffffffffu, rb[V - 1], 1);
+  T right = __shfl_down_sync(0xffffffffu, rb[0], 1);
+  if (lane == 0) left = hl;
+  if (lane == 31) right = hr;
 #pragma unroll
-      for (int e = 0; e < V; ++e) {
-        const int c = lane * V + e;
-        if (c >= st.sx0 && c < st.sx1) dstbuf[rowoff + st.x0 + c] = data[r * SW + c];
-      }
-    }
+  for (int e = 0; e < V; ++e) {
+    const T xm = e == 0 ? left : rb[e - 1], xp = e == V - 1 ? right : rb[e + 1];
+    o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
   }
-  if (ADJ && st.ring) {
-    // ring cells of the valid region
+  if constexpr (DEAD) {
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      if (dead & (1u << e)) o[e] = rb[e];
+  }
+}
+
+// Two steps over a strip in one pass.  hct / hct1: this lane's halo column
+// (x-1 for lane 0, x+1 for lane 31) at steps t and t+1, one entry per row;
+// m1 / m1n: row -1 at t / t+1; p0 / p0n: row R at t / t+1.
+template <typename T, bool DEAD>
+__device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1, int rows, int lane,
+                                           const Links<T> &a, const T (&m1)[VecOf<T>::V],
+                                           const T (&m1n)[VecOf<T>::V], const T (&p0)[VecOf<T>::V],
+                                           const T (&p0n)[VecOf<T>::V], uint32_t dead) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  T a0[V], b0[V], c0[V], a1[V], b1[V], n1[V], o[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    a0[e] = m1[e];
+    a1[e] = m1n[e];
+  }
+  vload(drow, false, b0);
+  if (rows > 1) {
+    vload(drow + SW, false, c0);
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) c0[e] = p0[e];
+  }
+  row_update<T, DEAD>(a0, b0, c0, hct[0], hct[0], lane, a, dead, b1);  // step t+1 of row 0
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    a0[e] = b0[e];
+    b0[e] = c0[e];
+  }
+#pragma unroll 2
+  for (int r = 1; r < rows; ++r) {
+    if (r + 1 < rows) {
+      vload(drow + (r + 1) * SW, false, c0);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) c0[e] = p0[e];
+    }
+    row_update<T, DEAD>(a0, b0, c0, hct[r], hct[r], lane, a, dead, n1);          // step t+1 of row r
+    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, dead, o);  // step t+2 of row r-1
+    vstore(drow + (r - 1) * SW, o);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-      const int c = lane * V + e, x = st.x0 + c;
-      const bool xin = x >= 1 && x <= nx && c >= st.sx0 && c < st.sx1;
-      if ((st.ring & (1 << SIDE_YM)) && xin && st.sy0 == 0) dstbuf[off + x] = rg.ym[e];
-      if ((st.ring & (1 << SIDE_YP)) && xin && st.sy1 == rows) dstbuf[(long)(ny + 1) * pitch + off + x] = rg.yp[e];
-    }
-    if ((st.ring & (1 << SIDE_XM)) && st.sx0 == 0) {
-      if (lane < rows && lane >= st.sy0 && lane < st.sy1) dstbuf[(long)(st.y0 + lane) * pitch + off] = rg.xm0;
-      if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
-        dstbuf[(long)(st.y0 + lane + 32) * pitch + off] = rg.xm1;
-    }
-    if ((st.ring & (1 << SIDE_XP)) && (nx - st.x0) < st.sx1) {
-      if (lane < rows && lane >= st.sy0 && lane < st.sy1)
-        dstbuf[(long)(st.y0 + lane) * pitch + off + nx + 1] = rg.xp0;
-      if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
-        dstbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1] = rg.xp1;
+      a1[e] = b1[e];
+      b1[e] = n1[e];
+      a0[e] = b0[e];
+      b0[e] = c0[e];
     }
   }
+  row_update<T, DEAD>(a1, b1, p0n, hct1[rows - 1], hct1[rows - 1], lane, a, dead, o);  // step t+2 of the last row
+  vstore(drow + (rows - 1) * SW, o);
+}
+
+// Advance one tile strip by k steps, two per exchange (an odd k ends with one
+// single step).  Called by every warp of the CTA with the same k.
+template <typename T>
+__device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, int warp, int src, int dst, int k,
+                               uint32_t &mbar_phase) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  const int lane = threadIdx.x & 31;
+  const int region = pair_region_elems((int)sizeof(T), kp.rmax);
+  T *wbase = reinterpret_cast<T *>(smem + kHeaderBytes);
+  T *data = wbase + (size_t)warp * region;
+  T *hc = data + (size_t)kp.rmax * SW;  // [4][32]: columns -1 and SW at step t, then at step t+1
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  const bool act = st.active;
+  const GridDev &gd = kp.grids[act ? st.g : 0];
+  const int nx = gd.nx, ny = gd.ny, rows = st.rows;
+  const long pitch = gd.pitch;
+  const int off = gd.off;
+  const T *srcbuf = reinterpret_cast<const T *>(gd.buf[src]);
+  T *dstbuf = reinterpret_cast<T *>(gd.buf[dst]);
+  const CUtensorMap *map_load = kp.maps + (size_t)st.g * 6 + src;
+  const CUtensorMap *map_store = kp.maps + (size_t)st.g * 6 + 3 + dst;
+  const Links<T> a{(T)gd.w[0], (T)gd.w[1], (T)gd.w[2], (T)gd.w[3], (T)gd.w[4]};
+
+  // neighbours (warps of this CTA: a tile has no other links) and the
+  // diagonal strips, which exist whenever both adjacent neighbours do
+  const int WX = kp.tile_wx;
+  auto nbw = [&](int s) { return act && st.link[s] >= 0 ? st.link[s] % kWarps : -1; };
+  const int wT = nbw(SIDE_YM), wB = nbw(SIDE_YP), wL = nbw(SIDE_XM), wR = nbw(SIDE_XP);
+  const int wTL = wT >= 0 && wL >= 0 ? warp - WX - 1 : -1;
+  const int wTR = wT >= 0 && wR >= 0 ? warp - WX + 1 : -1;
+  const int wBL = wB >= 0 && wL >= 0 ? warp + WX - 1 : -1;
+  const int wBR = wB >= 0 && wR >= 0 ? warp + WX + 1 : -1;
+  const int trows = kp.tile_rows;  // the strip above is a full strip
+  const int rowsB = wB >= 0 ? min(trows, ny + 1 - (st.y0 + rows)) : 0;
+  auto nbdata = [&](int w) { return wbase + (size_t)w * region; };
+
+  const int xl = st.x0 + lane * V;
+  T *drow = data + lane * V;
+  uint32_t dead = 0;
+#pragma unroll
+  for (int e = 0; e < V; ++e)
+    if (act && xl + e > nx) dead |= 1u << e;
+
+  // state-t cells around the strip (constant on sides without a neighbour)
+  T hm2[V], hm1[V], hp0[V], hp1[V];                   // rows -2, -1, R, R+1
+  T xm2 = T(0), xm1 = T(0), xp0 = T(0), xp1 = T(0);  // columns -2, -1, SW, SW+1 of row `lane`
+  T ctl = T(0), ctr = T(0), cbl = T(0), cbr = T(0);  // the diagonal cells
+  auto gval = [&](int y, int x) -> T {
+    return (x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+  };
+  if (act) {
+    fence_proxy_async_all();  // earlier generic writes before the async-proxy load
+    __syncwarp();
+    if (lane == 0) {
+      bulk_wait_read_all();  // previous strip's stores have read shared memory
+      mbar_expect_tx(&bars[warp], (uint32_t)(SW * kp.rmax * sizeof(T)));
+      tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int x = xl + e;
+      hm2[e] = wT < 0 ? gval(st.y0 - 2, x) : T(0);
+      hm1[e] = wT < 0 ? gval(st.y0 - 1, x) : T(0);
+      hp0[e] = wB < 0 ? gval(st.y0 + rows, x) : T(0);
+      hp1[e] = (wB < 0 || rowsB < 2) ? gval(st.y0 + rows + 1, x) : T(0);
+    }
+    if (lane < rows) {
+      const int y = st.y0 + lane;
+      if (wL < 0) {
+        xm2 = gval(y, st.x0 - 2);
+        xm1 = gval(y, st.x0 - 1);
+      }
+      if (wR < 0) {
+        xp0 = gval(y, st.x0 + SW);
+        xp1 = gval(y, st.x0 + SW + 1);
+      }
+    }
+    if (wTL < 0) ctl = gval(st.y0 - 1, st.x0 - 1);
+    if (wTR < 0) ctr = gval(st.y0 - 1, st.x0 + SW);
+    if (wBL < 0) cbl = gval(st.y0 + rows, st.x0 - 1);
+    if (wBR < 0) cbr = gval(st.y0 + rows, st.x0 + SW);
+    wait_mbar(&bars[warp], mbar_phase, kp);
+    mbar_phase ^= 1u;
+  }
+  __syncthreads();
+
+  const T *hct = hc + (lane == 31 ? 32 : 0);  // this lane's halo column at step t
+  const T *hct1 = hct + 64;                   // and at step t+1
+  const bool any_dead = __any_sync(0xffffffffu, dead != 0);
+  for (int t = 0; t < k; t += 2) {
+    const bool two = t + 1 < k;
+    T m1n[V], p0n[V];
+    if (act) {
+      // the neighbours' state-t cells, read in place
+      if (wT >= 0) {
+        const T *d = nbdata(wT) + lane * V;
+        vload(d + (trows - 2) * SW, false, hm2);
+        vload(d + (trows - 1) * SW, false, hm1);
+      }
+      if (wB >= 0) {
+        const T *d = nbdata(wB) + lane * V;
+        vload(d, false, hp0);
+        if (rowsB > 1) vload(d + SW, false, hp1);
+      }
+      if (lane < rows) {
+        if (wL >= 0) {
+          const T *d = nbdata(wL) + lane * SW;
+          xm2 = d[SW - 2];
+          xm1 = d[SW - 1];
+        }
+        if (wR >= 0) {
+          const T *d = nbdata(wR) + lane * SW;
+          xp0 = d[0];
+          xp1 = d[1];
+        }
+      }
+      if (wTL >= 0) ctl = nbdata(wTL)[(trows - 1) * SW + SW - 1];
+      if (wTR >= 0) ctr = nbdata(wTR)[(trows - 1) * SW];
+      if (wBL >= 0) cbl = nbdata(wBL)[SW - 1];
+      if (wBR >= 0) cbr = nbdata(wBR)[0];
+      if (two) {
+        // step t+1 on the ring around the strip
+        T own0 = T(0), ownl = T(0);
+        if (lane < rows) {
+          own0 = data[lane * SW];
+          ownl = data[lane * SW + SW - 1];
+        }
+        T up = __shfl_up_sync(0xffffffffu, xm1, 1), dn = __shfl_down_sync(0xffffffffu, xm1, 1);
+        if (lane == 0) up = ctl;
+        if (lane == rows - 1) dn = cbl;
+        const T l1 = wL >= 0 ? stencil(a, xm2, own0, up, xm1, dn) : xm1;
+        up = __shfl_up_sync(0xffffffffu, xp0, 1);
+        dn = __shfl_down_sync(0xffffffffu, xp0, 1);
+        if (lane == 0) up = ctr;
+        if (lane == rows - 1) dn = cbr;
+        const T r1 = wR >= 0 ? stencil(a, ownl, xp1, up, xp0, dn) : xp0;
+        if (lane < rows) {
+          hc[64 + lane] = l1;
+          hc[96 + lane] = r1;
+        }
+        T own[V];
+        if (wT >= 0) {
+          vload(drow, false, own);
+          row_update<T, true>(hm2, hm1, own, ctl, ctr, lane, a, dead, m1n);
+        } else {
+#pragma unroll
+          for (int e = 0; e < V; ++e) m1n[e] = hm1[e];
+        }
+        if (wB >= 0) {
+          vload(drow + (rows - 1) * SW, false, own);
+          row_update<T, true>(own, hp0, hp1, cbl, cbr, lane, a, dead, p0n);
+        } else {
+#pragma unroll
+          for (int e = 0; e < V; ++e) p0n[e] = hp0[e];
+        }
+      }
+      if (lane < rows) {
+        hc[lane] = xm1;
+        hc[32 + lane] = xp0;
+      }
+    }
+    __syncthreads();  // every strip has read its neighbours' state-t cells
+    if (act) {
+      if (two) {
+        if (any_dead)
+          sweep_pair<T, true>(drow, hct, hct1, rows, lane, a, hm1, m1n, hp0, p0n, dead);
+        else
+          sweep_pair<T, false>(drow, hct, hct1, rows, lane, a, hm1, m1n, hp0, p0n, dead);
+      } else {
+        RingAcc<T> rg{};
+        if (any_dead)
+          sweep_rows<T, false, true>(drow, hct, rows, lane, a, ExactW{}, false, xl, st.y0, hm1, hp0, dead, rg);
+        else
+          sweep_rows<T, false, false>(drow, hct, rows, lane, a, ExactW{}, false, xl, st.y0, hm1, hp0, dead, rg);
+      }
+    }
+    __syncthreads();  // every strip has written its new state
+  }
+  if (!act) return;
+  const RingAcc<T> rg{};
+  strip_store<T, false>(st, gd, data, map_store, dstbuf, lane, rg);
 }
 
 // Strip of slot `slot` in a band wave: columns strip j, row strip i of m.
@@ -724,7 +1025,10 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
     } else {
       for (int j = kp.job_off[blockIdx.x]; j < kp.job_off[blockIdx.x + 1]; ++j, ++seq) {
         const Strip st = tile_strip(kp, kp.jobs + 7 * j, warp, blockIdx.x * kWarps, SWc);
-        run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        if constexpr (MODE == MODE_TILES_PAIR)
+          run_strip_pair<T>(st, kp, smem, warp, src, dst, k, phase);
+        else
+          run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
         __syncthreads();
       }
       if (lane == 0) {
@@ -746,6 +1050,13 @@ int dtb_rows_max(j2d_dtype dt, size_t smem_optin, int warps) {
     const int rp = (r + 3) / 4 * 4;
     if (dtb_smem_bytes(elem, r, rp) <= smem_optin) return r;
   }
+  return 0;
+}
+
+int dtb_rows_max_pair(j2d_dtype dt, size_t smem_optin) {
+  const int elem = dt == J2D_F64 ? 8 : 4;
+  for (int r = 32; r >= 1; --r)
+    if (pair_smem_bytes(elem, r) <= smem_optin) return r;
   return 0;
 }
 
@@ -783,6 +1094,10 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   c.depth = rq.depth > 0 ? rq.depth : (dt == J2D_F64 ? 4 : 8);
   c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : (dt == J2D_F64 ? 4 : 2);
   if (algo == J2D_ALGO_RESIDENT) c.depth = (int)std::max<long>(rq.steps, 1);
+  if (algo == J2D_ALGO_TILES && dt == J2D_F32 && !rq.adjoint && rq.sweep_steps == 2) {
+    c.sweep = 2;
+    c.rows = dtb_rows_max_pair(dt, smem_optin);
+  }
   return c;
 }
 
@@ -843,6 +1158,9 @@ static void ensure(void *&p, size_t &cap, size_t need, cudaError_t &err) {
 
 template <typename T>
 static void *kernel_ptr(int mode, bool adj) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (mode == MODE_TILES_PAIR) return (void *)dtb_kernel<float, false, MODE_TILES_PAIR>;
+  }
   if (mode == MODE_BANDS) return adj ? (void *)dtb_kernel<T, true, MODE_BANDS> : (void *)dtb_kernel<T, false, MODE_BANDS>;
   return adj ? (void *)dtb_kernel<T, true, MODE_TILES> : (void *)dtb_kernel<T, false, MODE_TILES>;
 }
@@ -853,7 +1171,9 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   const int V = vec_of(dt), SW = 32 * V;
   const size_t elem = dt == J2D_F64 ? 8 : 4;
   const int ctas = r.cfg.ctas;
-  const int rmax = dtb_rows_max(dt, r.smem_optin, kWarps);
+  // two steps per sweep: FP32 tiles of the forward map
+  const bool pair = r.cfg.sweep == 2 && dt == J2D_F32 && r.cfg.algo == J2D_ALGO_TILES && !r.adjoint;
+  const int rmax = pair ? dtb_rows_max_pair(dt, r.smem_optin) : dtb_rows_max(dt, r.smem_optin, kWarps);
   const int rp = (rmax + 3) / 4 * 4;
   if (rmax < 2) { err = "shared memory too small"; return cudaErrorNotSupported; }
   const int mode = (r.cfg.algo == J2D_ALGO_TILES) ? MODE_TILES : MODE_BANDS;
@@ -1046,8 +1366,9 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   kp.mute_slot = r.mute_slot;
   kp.int_path = r.int_path;
 
-  const size_t smem = dtb_smem_bytes((int)elem, rmax, rp);
-  void *fn = dt == J2D_F64 ? kernel_ptr<double>(mode, r.adjoint) : kernel_ptr<float>(mode, r.adjoint);
+  const size_t smem = pair ? pair_smem_bytes((int)elem, rmax) : dtb_smem_bytes((int)elem, rmax, rp);
+  const int kmode = pair ? MODE_TILES_PAIR : mode;
+  void *fn = dt == J2D_F64 ? kernel_ptr<double>(kmode, r.adjoint) : kernel_ptr<float>(kmode, r.adjoint);
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
     err = "shared memory attribute";
     return e;

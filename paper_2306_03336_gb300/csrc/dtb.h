@@ -17,6 +17,7 @@ struct DtbRequest {
   int ctas = 0;
   long steps = 0;
   bool adjoint = false;
+  int sweep_steps = 2;  // TILES, FP32 forward: steps per sweep (J2D_OPT_SWEEP_STEPS)
 };
 
 // Everything one temporally blocked run needs.
@@ -49,6 +50,8 @@ struct DtbState {
 
 // Largest rows per warp strip that fit in shared memory.
 int dtb_rows_max(j2d_dtype dt, size_t smem_optin, int warps);
+// The same for the two-steps-per-sweep tiles (no mailboxes; at most 32 rows).
+int dtb_rows_max_pair(j2d_dtype dt, size_t smem_optin);
 
 DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, size_t smem_optin,
                      const DtbRequest &rq);

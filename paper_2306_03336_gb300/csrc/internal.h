@@ -28,6 +28,7 @@ struct DtbConfig {
   int tile_wx = 4;              // TILES: strips across a tile
   int ctas = 0;                 // persistent grid size
   int rows = 0;                 // rows per warp strip
+  int sweep = 1;                // TILES, FP32 forward: time steps per shared-memory sweep (1 or 2)
 };
 
 // Device scratch for the temporally blocked kernels.
