@@ -679,14 +679,12 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
     a0[e] = b0[e];
     b0[e] = c0[e];
   }
-#pragma unroll 2
-  for (int r = 1; r < rows; ++r) {
-    if (r + 1 < rows) {
-      vload(drow + (r + 1) * SW, false, c0);
-    } else {
-#pragma unroll
-      for (int e = 0; e < V; ++e) c0[e] = p0[e];
-    }
+  // both windows advance by one row per iteration: unrolling by their period
+  // (3) lets the compiler rename the registers instead of moving them; the
+  // last row is peeled so that the loop loads the next row unconditionally
+#pragma unroll 3
+  for (int r = 1; r < rows - 1; ++r) {
+    vload(drow + (r + 1) * SW, false, c0);
     row_update<T, DEAD>(a0, b0, c0, hct[r], hct[r], lane, a, dead, n1);          // step t+1 of row r
     row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, dead, o);  // step t+2 of row r-1
     vstore(drow + (r - 1) * SW, o);
@@ -696,6 +694,17 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
       b1[e] = n1[e];
       a0[e] = b0[e];
       b0[e] = c0[e];
+    }
+  }
+  if (rows > 1) {
+    const int r = rows - 1;
+    row_update<T, DEAD>(a0, b0, p0, hct[r], hct[r], lane, a, dead, n1);          // step t+1 of the last row
+    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, dead, o);  // step t+2 of row R-2
+    vstore(drow + (r - 1) * SW, o);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      a1[e] = b1[e];
+      b1[e] = n1[e];
     }
   }
   row_update<T, DEAD>(a1, b1, p0n, hct1[rows - 1], hct1[rows - 1], lane, a, dead, o);  // step t+2 of the last row
