@@ -349,7 +349,9 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
             if hbm:
                 ent["onestep_frac_hbm"] = round(k1 * 8 / hbm, 3)
             ent["best_frac_fp32_pipe"] = round(k2 / (fma32 / 5 / 1e9), 3)
-            ent["best_frac_smem"] = round(k2 * 8 / smem, 3)
+            # one 4-byte load and store per cell per sweep; a sweep advances `sweep` steps
+            sweep = int(dict(kv.split("=") for kv in best.split()).get("sweep", "1"))
+            ent["best_frac_smem"] = round(k2 * 8 / sweep / smem, 3)
             got = p.view(b).double()
             ent["max_rel_err_vs_fp64"] = float(((got - ref64).abs().max() / ref64.abs().max()).item())
             del ref64
