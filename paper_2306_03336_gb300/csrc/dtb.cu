@@ -626,13 +626,15 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
 // a neighbour (ring, overlapped tile halo) keep the values read at the strip's
 // load, as in the single-step exchange.
 
-// One row of a sweep: new values from the old rows above (ra), at (rb) and
-// below (rc); lane 0 takes x-1 from hl, lane 31 takes x+1 from hr; dead
-// columns keep their value.  The same evaluation as sweep_row().
+// One row (logical row y) of a sweep: new values from the old rows above
+// (ra), at (rb) and below (rc); lane 0 takes x-1 from hl, lane 31 takes x+1
+// from hr; dead columns keep their value.  The same evaluation as sweep_row()
+// (FP64: the integer path on the cells exact_cell() selects).
 template <typename T, bool DEAD>
 __device__ __forceinline__ void row_update(const T (&ra)[VecOf<T>::V], const T (&rb)[VecOf<T>::V],
                                            const T (&rc)[VecOf<T>::V], T hl, T hr, int lane, const Links<T> &a,
-                                           uint32_t dead, T (&o)[VecOf<T>::V]) {
+                                           const ExactW &u, bool ipath, int xl, int y, uint32_t dead,
+                                           T (&o)[VecOf<T>::V]) {
   constexpr int V = VecOf<T>::V;
   T left = __shfl_up_sync(0xffffffffu, rb[V - 1], 1);
   T right = __shfl_down_sync(0xffffffffu, rb[0], 1);
@@ -641,7 +643,10 @@ __device__ __forceinline__ void row_update(const T (&ra)[VecOf<T>::V], const T (
 #pragma unroll
   for (int e = 0; e < V; ++e) {
     const T xm = e == 0 ? left : rb[e - 1], xp = e == V - 1 ? right : rb[e + 1];
-    o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
+    if constexpr (std::is_same<T, double>::value)
+      o[e] = stencil_cell(a, u, exact_cell(xl + e, y, ipath), xm, xp, ra[e], rb[e], rc[e]);
+    else
+      o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
   }
   if constexpr (DEAD) {
 #pragma unroll
@@ -655,7 +660,8 @@ __device__ __forceinline__ void row_update(const T (&ra)[VecOf<T>::V], const T (
 // m1 / m1n: row -1 at t / t+1; p0 / p0n: row R at t / t+1.
 template <typename T, bool DEAD>
 __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1, int rows, int lane,
-                                           const Links<T> &a, const T (&m1)[VecOf<T>::V],
+                                           const Links<T> &a, const ExactW &u, bool ip, int xl, int y0,
+                                           const T (&m1)[VecOf<T>::V],
                                            const T (&m1n)[VecOf<T>::V], const T (&p0)[VecOf<T>::V],
                                            const T (&p0n)[VecOf<T>::V], uint32_t dead) {
   constexpr int V = VecOf<T>::V;
@@ -673,20 +679,22 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
 #pragma unroll
     for (int e = 0; e < V; ++e) c0[e] = p0[e];
   }
-  row_update<T, DEAD>(a0, b0, c0, hct[0], hct[0], lane, a, dead, b1);  // step t+1 of row 0
+  row_update<T, DEAD>(a0, b0, c0, hct[0], hct[0], lane, a, u, ip, xl, y0, dead, b1);  // step t+1 of row 0
 #pragma unroll
   for (int e = 0; e < V; ++e) {
     a0[e] = b0[e];
     b0[e] = c0[e];
   }
   // both windows advance by one row per iteration: unrolling by their period
-  // (3) lets the compiler rename the registers instead of moving them; the
+  // (3) lets the compiler rename the registers instead of moving them (FP32;
+  // the FP64 rows, with the integer path, do not fit three to a body); the
   // last row is peeled so that the loop loads the next row unconditionally
-#pragma unroll 3
+  constexpr int kUnroll = sizeof(T) == 4 ? 3 : 1;
+#pragma unroll kUnroll
   for (int r = 1; r < rows - 1; ++r) {
     vload(drow + (r + 1) * SW, false, c0);
-    row_update<T, DEAD>(a0, b0, c0, hct[r], hct[r], lane, a, dead, n1);          // step t+1 of row r
-    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, dead, o);  // step t+2 of row r-1
+    row_update<T, DEAD>(a0, b0, c0, hct[r], hct[r], lane, a, u, ip, xl, y0 + r, dead, n1);  // step t+1 of row r
+    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, u, ip, xl, y0 + r - 1, dead, o);  // t+2, row r-1
     vstore(drow + (r - 1) * SW, o);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -698,8 +706,8 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
   }
   if (rows > 1) {
     const int r = rows - 1;
-    row_update<T, DEAD>(a0, b0, p0, hct[r], hct[r], lane, a, dead, n1);          // step t+1 of the last row
-    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, dead, o);  // step t+2 of row R-2
+    row_update<T, DEAD>(a0, b0, p0, hct[r], hct[r], lane, a, u, ip, xl, y0 + r, dead, n1);  // step t+1 of the last row
+    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, u, ip, xl, y0 + r - 1, dead, o);  // t+2, row R-2
     vstore(drow + (r - 1) * SW, o);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -707,7 +715,7 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
       b1[e] = n1[e];
     }
   }
-  row_update<T, DEAD>(a1, b1, p0n, hct1[rows - 1], hct1[rows - 1], lane, a, dead, o);  // step t+2 of the last row
+  row_update<T, DEAD>(a1, b1, p0n, hct1[rows - 1], hct1[rows - 1], lane, a, u, ip, xl, y0 + rows - 1, dead, o);  // t+2, last row
   vstore(drow + (rows - 1) * SW, o);
 }
 
@@ -734,6 +742,16 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
   const CUtensorMap *map_load = kp.maps + (size_t)st.g * 6 + src;
   const CUtensorMap *map_store = kp.maps + (size_t)st.g * 6 + 3 + dst;
   const Links<T> a{(T)gd.w[0], (T)gd.w[1], (T)gd.w[2], (T)gd.w[3], (T)gd.w[4]};
+  ExactW u{};
+  if constexpr (std::is_same<T, double>::value) u = exact_weights(a);
+  const bool ip = kp.int_path != 0;
+  // a halo-column cell (logical x, y), evaluated as its owner evaluates it
+  auto cell = [&](int x, int y, T xm, T xp, T ym, T c, T yp) -> T {
+    if constexpr (std::is_same<T, double>::value)
+      return stencil_cell(a, u, exact_cell(x, y, ip), xm, xp, ym, c, yp);
+    else
+      return stencil(a, xm, xp, ym, c, yp);
+  };
 
   // neighbours (warps of this CTA: a tile has no other links) and the
   // diagonal strips, which exist whenever both adjacent neighbours do
@@ -842,12 +860,12 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
         T up = __shfl_up_sync(0xffffffffu, xm1, 1), dn = __shfl_down_sync(0xffffffffu, xm1, 1);
         if (lane == 0) up = ctl;
         if (lane == rows - 1) dn = cbl;
-        const T l1 = wL >= 0 ? stencil(a, xm2, own0, up, xm1, dn) : xm1;
+        const T l1 = wL >= 0 ? cell(st.x0 - 1, st.y0 + lane, xm2, own0, up, xm1, dn) : xm1;
         up = __shfl_up_sync(0xffffffffu, xp0, 1);
         dn = __shfl_down_sync(0xffffffffu, xp0, 1);
         if (lane == 0) up = ctr;
         if (lane == rows - 1) dn = cbr;
-        const T r1 = wR >= 0 ? stencil(a, ownl, xp1, up, xp0, dn) : xp0;
+        const T r1 = wR >= 0 ? cell(st.x0 + SW, st.y0 + lane, ownl, xp1, up, xp0, dn) : xp0;
         if (lane < rows) {
           hc[64 + lane] = l1;
           hc[96 + lane] = r1;
@@ -855,14 +873,14 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
         T own[V];
         if (wT >= 0) {
           vload(drow, false, own);
-          row_update<T, true>(hm2, hm1, own, ctl, ctr, lane, a, dead, m1n);
+          row_update<T, true>(hm2, hm1, own, ctl, ctr, lane, a, u, ip, xl, st.y0 - 1, dead, m1n);
         } else {
 #pragma unroll
           for (int e = 0; e < V; ++e) m1n[e] = hm1[e];
         }
         if (wB >= 0) {
           vload(drow + (rows - 1) * SW, false, own);
-          row_update<T, true>(own, hp0, hp1, cbl, cbr, lane, a, dead, p0n);
+          row_update<T, true>(own, hp0, hp1, cbl, cbr, lane, a, u, ip, xl, st.y0 + rows, dead, p0n);
         } else {
 #pragma unroll
           for (int e = 0; e < V; ++e) p0n[e] = hp0[e];
@@ -877,15 +895,15 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
     if (act) {
       if (two) {
         if (any_dead)
-          sweep_pair<T, true>(drow, hct, hct1, rows, lane, a, hm1, m1n, hp0, p0n, dead);
+          sweep_pair<T, true>(drow, hct, hct1, rows, lane, a, u, ip, xl, st.y0, hm1, m1n, hp0, p0n, dead);
         else
-          sweep_pair<T, false>(drow, hct, hct1, rows, lane, a, hm1, m1n, hp0, p0n, dead);
+          sweep_pair<T, false>(drow, hct, hct1, rows, lane, a, u, ip, xl, st.y0, hm1, m1n, hp0, p0n, dead);
       } else {
         RingAcc<T> rg{};
         if (any_dead)
-          sweep_rows<T, false, true>(drow, hct, rows, lane, a, ExactW{}, false, xl, st.y0, hm1, hp0, dead, rg);
+          sweep_rows<T, false, true>(drow, hct, rows, lane, a, u, ip, xl, st.y0, hm1, hp0, dead, rg);
         else
-          sweep_rows<T, false, false>(drow, hct, rows, lane, a, ExactW{}, false, xl, st.y0, hm1, hp0, dead, rg);
+          sweep_rows<T, false, false>(drow, hct, rows, lane, a, u, ip, xl, st.y0, hm1, hp0, dead, rg);
       }
     }
     __syncthreads();  // every strip has written its new state
@@ -1103,6 +1121,8 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   c.depth = rq.depth > 0 ? rq.depth : (dt == J2D_F64 ? 4 : 8);
   c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : (dt == J2D_F64 ? 4 : 2);
   if (algo == J2D_ALGO_RESIDENT) c.depth = (int)std::max<long>(rq.steps, 1);
+  // two steps per sweep: FP32 only (FP64 tiles measured 11% slower with it:
+  // the integer path of four cells in flight spills at 128 registers)
   if (algo == J2D_ALGO_TILES && dt == J2D_F32 && !rq.adjoint && rq.sweep_steps == 2) {
     c.sweep = 2;
     c.rows = dtb_rows_max_pair(dt, smem_optin);
