@@ -80,9 +80,10 @@ typedef enum {
                              buffers and step count) and replayed by later identical calls */
   J2D_OPT_TIMING = 7,     /* 1 = runs record CUDA events around their stencil kernels, read
                              by j2d5pt_kernel_time (ignored for graph replays) */
-  J2D_OPT_FAULT_INJECT = 8, /* testing: 1 = in the resident and bands kernels, the first strip
-                               never publishes its step counter to other CTAs, so its neighbours'
-                               bounded waits expire and the run reports J2D_ERR_TIMEOUT */
+  J2D_OPT_FAULT_INJECT = 8, /* testing: 1 = in the resident and bands kernels, one strip with a
+                               neighbour in another CTA never publishes its step counter to other
+                               CTAs, so that neighbour's bounded waits expire and the run reports
+                               J2D_ERR_TIMEOUT */
   J2D_OPT_INT_PATH = 9,     /* FP64: 1 (default) = the cells j2d5pt_arith_info selects are
                                evaluated on the integer pipes; 0 = every cell takes the FMA
                                chain on the FP64 pipe.  Ignored for FP32. */

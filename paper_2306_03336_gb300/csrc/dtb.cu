@@ -69,6 +69,7 @@ struct KParams {
   int rounds, depth, last_depth, src0;
   int rmax, rp;             // strip rows (max), mailbox column length
   int m;                    // BANDS: strips per column (per-wave value in the job)
+  int bx;                   // BANDS: CTA block of bx x (16/bx) strips, 0 = 16 strips down a column
   int tile_wx, tile_rows;   // TILES
   int *status;
   int *barrier;             // grid barrier counter
@@ -920,9 +921,25 @@ __device__ Strip band_strip(const KParams &kp, const int *wave, int slot, int SW
   const int nx = gd.nx, ny = gd.ny;
   const int by0 = wave[0], by1 = wave[1], vy0 = wave[2], vy1 = wave[3], m = wave[4];
   const int ncs = (nx + SWc - 1) / SWc;
-  st.active = slot < ncs * m;
+  // strip (column j, row i) of slot: either consecutive slots run down a
+  // column (bx = 0), or each CTA holds a block of bx columns x 16/bx rows, so
+  // that most x neighbours share the CTA as well
+  const int BX = kp.bx > 0 ? kp.bx : 1, BY = kWarps / BX, nbx = (ncs + BX - 1) / BX;
+  int j, i;
+  if (kp.bx == 0) {
+    j = slot / m;
+    i = slot % m;
+    st.active = slot < ncs * m;
+  } else {
+    const int b = slot / kWarps, w = slot % kWarps;
+    j = (b % nbx) * BX + w % BX;
+    i = (b / nbx) * BY + w / BX;
+    st.active = j < ncs && i < m;
+  }
   if (!st.active) return st;
-  const int j = slot / m, i = slot % m;
+  auto slot_of = [&](int jj, int ii) {
+    return kp.bx == 0 ? jj * m + ii : ((ii / BY) * nbx + jj / BX) * kWarps + (ii % BY) * BX + jj % BX;
+  };
   // rows spread evenly: strip i gets one of the `extra` leftover rows when
   // floor((i+1)*extra/m) steps up, so every run of consecutive strips (a CTA)
   // carries the same work to within one row
@@ -939,10 +956,10 @@ __device__ Strip band_strip(const KParams &kp, const int *wave, int slot, int SW
   if (ylast == ny) st.ring |= 1 << SIDE_YP;
   if (st.x0 == 1) st.ring |= 1 << SIDE_XM;
   if (st.x0 <= nx && nx <= st.x0 + SWc - 1) st.ring |= 1 << SIDE_XP;
-  st.link[SIDE_YM] = i > 0 ? slot - 1 : LINK_CONST;
-  st.link[SIDE_YP] = i < m - 1 ? slot + 1 : LINK_CONST;
-  st.link[SIDE_XM] = j > 0 ? slot - m : LINK_CONST;
-  st.link[SIDE_XP] = j < ncs - 1 ? slot + m : LINK_CONST;
+  st.link[SIDE_YM] = i > 0 ? slot_of(j, i - 1) : LINK_CONST;
+  st.link[SIDE_YP] = i < m - 1 ? slot_of(j, i + 1) : LINK_CONST;
+  st.link[SIDE_XM] = j > 0 ? slot_of(j - 1, i) : LINK_CONST;
+  st.link[SIDE_XP] = j < ncs - 1 ? slot_of(j + 1, i) : LINK_CONST;
   st.sy0 = max(vy0 - st.y0, 0);
   st.sy1 = min(vy1 - st.y0, st.rows);
   if (st.sy1 < st.sy0) st.sy1 = st.sy0;
@@ -1100,6 +1117,34 @@ static bool resident_fit(const GridDesc &g, int sw, int ctas, int rmax, int *m_o
   return true;
 }
 
+// Strips per column for one grid of ncs strip columns on `ctas` CTAs when
+// each CTA holds a block of bx columns x 16/bx rows of strips (bx = 0:
+// consecutive slots run down the columns); 0 if the grid is too wide.
+static int strips_per_column(int ncs, int ny, int ctas, int bx) {
+  if (bx == 0) {
+    const long slots = (long)ctas * kWarps;
+    return ncs > slots ? 0 : (int)std::min<long>(slots / ncs, ny);
+  }
+  const int nbx = (ncs + bx - 1) / bx;
+  return nbx > ctas ? 0 : std::min((kWarps / bx) * (ctas / nbx), ny);
+}
+
+// The strip mapping of RESIDENT / BANDS: the most strips per column (the
+// least work per warp); among equals, the CTA block with the fewest strip
+// edges leaving the CTA (4x4, then 8x2, then 2x8, then columns).
+static int choose_bx(int ncs, int ny, int ctas, int *m_out) {
+  int best_bx = 0, best_m = strips_per_column(ncs, ny, ctas, 0);
+  for (int bx : {2, 8, 4}) {
+    const int m = strips_per_column(ncs, ny, ctas, bx);
+    if (m > 0 && m >= best_m) {
+      best_bx = bx;
+      best_m = m;
+    }
+  }
+  *m_out = best_m;
+  return best_bx;
+}
+
 DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, size_t smem_optin,
                      const DtbRequest &rq) {
   DtbConfig c;
@@ -1215,6 +1260,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   if (r.cfg.algo == J2D_ALGO_RESIDENT) {
     int m = 0;
     if (!resident_fit(grids[0], SW, ctas, rmax, &m)) { err = "grid does not fit on chip"; return cudaErrorNotSupported; }
+    kp.bx = choose_bx((grids[0].nx + SW - 1) / SW, grids[0].ny, ctas, &m);
     depth = last = (int)r.steps;
     rounds = 1;
     jobs = {1, grids[0].ny + 1, 1, grids[0].ny + 1, m};
@@ -1227,7 +1273,8 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
       const int ncs = (g.nx + SW - 1) / SW;
       const long slots = (long)ctas * kWarps;
       if (ncs > slots) { err = "grid too wide for one band"; return cudaErrorNotSupported; }
-      const int m = (int)std::min<long>(slots / ncs, g.ny);
+      int m = 0;
+      kp.bx = choose_bx(ncs, g.ny, ctas, &m);
       const int hb = m * rmax;
       auto cv = cover(g.ny, hb, depth);
       if (cv.empty() || cv.back() != g.ny + 1) { err = "band too short for the temporal depth"; return cudaErrorNotSupported; }
@@ -1392,7 +1439,10 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   kp.gflags = reinterpret_cast<int *>(sc + 256);
   kp.gslots = sc + 256 + nslots * sizeof(int);
   kp.timeout_ns = r.timeout_ns;
-  kp.mute_slot = r.mute_slot;
+  // fault injection mutes a strip with a neighbour in another CTA: the first
+  // slot when slots run down the columns, else the last column of the first
+  // CTA block
+  kp.mute_slot = r.mute_slot < 0 ? -1 : (kp.bx > 0 ? kp.bx - 1 : 0);
   kp.int_path = r.int_path;
 
   const size_t smem = pair ? pair_smem_bytes((int)elem, rmax) : dtb_smem_bytes((int)elem, rmax, rp);

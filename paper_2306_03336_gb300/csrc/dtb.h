@@ -35,7 +35,7 @@ struct DtbRun {
   int sms = 0;
   size_t smem_optin = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the kernel if set
-  int mute_slot = -1;                         // fault injection (J2D_OPT_FAULT_INJECT)
+  int mute_slot = -1;                         // fault injection (J2D_OPT_FAULT_INJECT): >= 0 = on
   int int_path = 0;                           // FP64 integer path on (J2D_OPT_INT_PATH)
 };
 
