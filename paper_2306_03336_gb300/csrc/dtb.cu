@@ -171,6 +171,12 @@ __device__ void grid_barrier(const KParams &kp, int &epoch) {
 
 // ---- strips ----------------------------------------------------------------
 
+// A strip's next load, prefetched into L2 while the current strip runs.
+struct Prefetch {
+  const CUtensorMap *map = nullptr;  // none when null
+  int x = 0, y = 0;
+};
+
 struct Strip {
   int g;              // grid index
   int x0, y0, rows;   // logical coordinates of the first cell; number of rows
@@ -390,7 +396,7 @@ __device__ void strip_store(const Strip &st, const GridDev &gd, const T *data, c
 // barrier per step instead.
 template <typename T, bool ADJ>
 __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int warp, int slot, int src, int dst,
-                          int k, int base, uint32_t &mbar_phase) {
+                          int k, int base, uint32_t &mbar_phase, const Prefetch &pf = Prefetch{}) {
   constexpr int V = VecOf<T>::V;
   constexpr int SW = 32 * V;
   using L = WarpLayout<T>;
@@ -552,6 +558,7 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
     }
     wait_mbar(&bars[warp], mbar_phase, kp);
     mbar_phase ^= 1u;
+    if (pf.map && lane == 0) tma_prefetch_2d(pf.map, pf.x, pf.y);
     if (ADJ && dead) {
 #pragma unroll
       for (int e = 0; e < V; ++e)
@@ -1067,12 +1074,26 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
         grid_barrier(kp, epoch);
       }
     } else {
-      for (int j = kp.job_off[blockIdx.x]; j < kp.job_off[blockIdx.x + 1]; ++j, ++seq) {
+      const int jend = kp.job_off[blockIdx.x + 1];
+      for (int j = kp.job_off[blockIdx.x]; j < jend; ++j, ++seq) {
         const Strip st = tile_strip(kp, kp.jobs + 7 * j, warp, blockIdx.x * kWarps, SWc);
-        if constexpr (MODE == MODE_TILES_PAIR)
+        if constexpr (MODE == MODE_TILES_PAIR) {
           run_strip_pair<T>(st, kp, smem, warp, src, dst, k, phase);
-        else
-          run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        } else {
+          // this warp's strip of the CTA's next tile (same round, same source)
+          // goes into L2 while this tile runs (+1% FP64 tiles; the two-step
+          // FP32 kernel has no registers to spare for it: -2% there)
+          Prefetch pf;
+          if (j + 1 < jend) {
+            const Strip nst = tile_strip(kp, kp.jobs + 7 * (j + 1), warp, blockIdx.x * kWarps, SWc);
+            if (nst.active) {
+              pf.map = kp.maps + (size_t)nst.g * 6 + src;
+              pf.x = kp.grids[nst.g].off + nst.x0;
+              pf.y = nst.y0;
+            }
+          }
+          run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase, pf);
+        }
         __syncthreads();
       }
       if (lane == 0) {
