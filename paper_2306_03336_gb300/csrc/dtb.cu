@@ -1074,8 +1074,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
         grid_barrier(kp, epoch);
       }
     } else {
-      const int jend = kp.job_off[blockIdx.x + 1];
-      for (int j = kp.job_off[blockIdx.x]; j < jend; ++j, ++seq) {
+      for (int j = kp.job_off[blockIdx.x]; j < kp.job_off[blockIdx.x + 1]; ++j, ++seq) {
         const Strip st = tile_strip(kp, kp.jobs + 7 * j, warp, blockIdx.x * kWarps, SWc);
         if constexpr (MODE == MODE_TILES_PAIR) {
           run_strip_pair<T>(st, kp, smem, warp, src, dst, k, phase);
@@ -1084,7 +1083,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
           // goes into L2 while this tile runs (+1% FP64 tiles; the two-step
           // FP32 kernel has no registers to spare for it: -2% there)
           Prefetch pf;
-          if (j + 1 < jend) {
+          if (j + 1 < kp.job_off[blockIdx.x + 1]) {
             const Strip nst = tile_strip(kp, kp.jobs + 7 * (j + 1), warp, blockIdx.x * kWarps, SWc);
             if (nst.active) {
               pf.map = kp.maps + (size_t)nst.g * 6 + src;
