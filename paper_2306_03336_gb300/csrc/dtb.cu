@@ -38,6 +38,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <functional>
+#include <queue>
 #include <cstring>
 #include <type_traits>
 
@@ -51,6 +53,12 @@ constexpr int kThreads = kWarps * 32;
 enum { SIDE_YM = 0, SIDE_YP = 1, SIDE_XM = 2, SIDE_XP = 3 };
 enum { LINK_CONST = -1, LINK_ZERO = -2 };
 enum { MODE_BANDS = 0, MODE_TILES = 1, MODE_TILES_PAIR = 2 };
+// A tile job: grid, tile origin (x, y), valid core [vx0, vx1) x [vy0, vy1),
+// first warp, strips across and down (only the strips inside the grid: a
+// CTA runs a group of partial tiles side by side), and in the first tile of
+// a group the number of tiles in the group (so that a group is read with its
+// first record, no extra indirection).
+constexpr int kTileInts = 11;
 
 // Per-grid data the kernel reads from global memory.
 struct GridDev {
@@ -63,8 +71,8 @@ struct GridDev {
 struct KParams {
   const GridDev *grids;
   const CUtensorMap *maps;  // per grid: load maps of buf[0..2], store maps of buf[0..2]
-  const int *jobs;          // BANDS: 5 ints per wave; TILES: 7 ints per tile
-  const int *job_off;       // TILES: CTA b processes jobs [job_off[b], job_off[b+1])
+  const int *jobs;          // BANDS: 5 ints per wave; TILES: kTileInts ints per tile
+  const int *job_off;       // TILES: CTA b processes tiles [job_off[b], job_off[b+1]), group by group
   int njobs;                // waves (BANDS) or tiles (TILES) per round
   int rounds, depth, last_depth, src0;
   int rmax, rp;             // strip rows (max), mailbox column length
@@ -184,6 +192,7 @@ struct Strip {
   int ring;           // bit per side: that side is the domain ring
   int sy0, sy1;       // rows to store (strip-relative)
   int sx0, sx1;       // columns to store (strip-relative)
+  int tw;             // TILES: strips across the strip's tile
   bool active;
 };
 
@@ -763,7 +772,7 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
 
   // neighbours (warps of this CTA: a tile has no other links) and the
   // diagonal strips, which exist whenever both adjacent neighbours do
-  const int WX = kp.tile_wx;
+  const int WX = st.tw;
   auto nbw = [&](int s) { return act && st.link[s] >= 0 ? st.link[s] % kWarps : -1; };
   const int wT = nbw(SIDE_YM), wB = nbw(SIDE_YP), wL = nbw(SIDE_XM), wR = nbw(SIDE_XP);
   const int wTL = wT >= 0 && wL >= 0 ? warp - WX - 1 : -1;
@@ -975,14 +984,17 @@ __device__ Strip band_strip(const KParams &kp, const int *wave, int slot, int SW
   return st;
 }
 
-// Strip of warp w of a tile: wx across, wy down; rows per strip kp.tile_rows.
+// Strip of warp w (counted from the tile's first warp) of a tile of WX x WY
+// strips; rows per strip kp.tile_rows.
 __device__ Strip tile_strip(const KParams &kp, const int *tile, int w, int cta_slot0, int SWc) {
   Strip st{};
   const int g = tile[0], tx0 = tile[1], ty0 = tile[2], vx0 = tile[3], vx1 = tile[4], vy0 = tile[5], vy1 = tile[6];
+  const int WX = tile[8], WY = tile[9];
+  cta_slot0 += tile[7];
   const GridDev &gd = kp.grids[g];
   const int nx = gd.nx, ny = gd.ny;
-  const int WX = kp.tile_wx, WY = kWarps / WX;
   const int wx = w % WX, wy = w / WX;
+  st.tw = WX;
   st.g = g;
   st.x0 = tx0 + wx * SWc;
   st.y0 = ty0 + wy * kp.tile_rows;
@@ -1013,6 +1025,19 @@ __device__ Strip tile_strip(const KParams &kp, const int *tile, int w, int cta_s
   // is stored whole with TMA; the store map clips beyond column nx
   if (st.sx0 == 0 && st.x0 + st.sx1 >= min(vx1, nx + 1) && (vx1 > nx || st.sx1 == SWc)) st.sx1 = SWc;
   return st;
+}
+
+// This warp's strip in the tile group starting at job j (inactive if no tile
+// of the group uses it); count = the group's number of tiles.
+__device__ Strip group_strip(const KParams &kp, int j, int warp, int cta_slot0, int SWc, int &count) {
+  const int *t0 = kp.jobs + (size_t)kTileInts * j;
+  count = t0[10];
+  for (int i = 0; i < count; ++i) {
+    const int *t = t0 + (size_t)kTileInts * i;
+    const int w = warp - t[7];
+    if (w >= 0 && w < t[8] * t[9]) return tile_strip(kp, t, w, cta_slot0, SWc);
+  }
+  return Strip{};
 }
 
 // Ring copy for every grid of a run in one launch: block (g, d) copies the
@@ -1074,8 +1099,9 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
         grid_barrier(kp, epoch);
       }
     } else {
-      for (int j = kp.job_off[blockIdx.x]; j < kp.job_off[blockIdx.x + 1]; ++j, ++seq) {
-        const Strip st = tile_strip(kp, kp.jobs + 7 * j, warp, blockIdx.x * kWarps, SWc);
+      int cnt = 1;
+      for (int j = kp.job_off[blockIdx.x]; j < kp.job_off[blockIdx.x + 1]; j += cnt, ++seq) {
+        const Strip st = group_strip(kp, j, warp, blockIdx.x * kWarps, SWc, cnt);
         if constexpr (MODE == MODE_TILES_PAIR) {
           run_strip_pair<T>(st, kp, smem, warp, src, dst, k, phase);
         } else {
@@ -1083,8 +1109,9 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
           // goes into L2 while this tile runs (+1% FP64 tiles; the two-step
           // FP32 kernel has no registers to spare for it: -2% there)
           Prefetch pf;
-          if (j + 1 < kp.job_off[blockIdx.x + 1]) {
-            const Strip nst = tile_strip(kp, kp.jobs + 7 * (j + 1), warp, blockIdx.x * kWarps, SWc);
+          if (j + cnt < kp.job_off[blockIdx.x + 1]) {
+            int ncnt;
+            const Strip nst = group_strip(kp, j + cnt, warp, blockIdx.x * kWarps, SWc, ncnt);
             if (nst.active) {
               pf.map = kp.maps + (size_t)nst.g * 6 + src;
               pf.x = kp.grids[nst.g].off + nst.x0;
@@ -1275,7 +1302,9 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   if (mode == MODE_BANDS && !single) { err = "bands/resident need a single grid"; return cudaErrorNotSupported; }
 
   KParams kp{};
-  std::vector<int> jobs;
+  std::vector<int> jobs, job_off;
+  std::vector<long> tkey;
+  bool tiles_cached = false;
   int depth = r.cfg.depth, rounds = 1, last = (int)r.steps;
   if (r.cfg.algo == J2D_ALGO_RESIDENT) {
     int m = 0;
@@ -1309,7 +1338,17 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
       const int trows = rmax;
       const int tw = wx * SW, th = wy * trows;
       const int gx = (depth + V - 1) / V * V;
-      for (size_t gi = 0; gi < grids.size(); ++gi) {
+      tkey = {ctas, wx, rmax, depth, (long)grids.size()};
+      for (const GridDesc &g : grids) {
+        tkey.push_back(g.nx);
+        tkey.push_back(g.ny);
+      }
+      tiles_cached = tkey == S.tiles_key;
+      if (tiles_cached) {
+        jobs = S.tiles_jobs;
+        job_off = S.tiles_off;
+      }
+      for (size_t gi = 0; gi < grids.size() && !tiles_cached; ++gi) {
         const GridDesc &g = grids[gi];
         // a grid that fits one tile needs no overlapped halo; otherwise the
         // halo of depth k must leave each tile a valid core
@@ -1319,51 +1358,94 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
           return cudaErrorNotSupported;
         }
         for (size_t a = 0; a + 2 < cy.size(); a += 3)
-          for (size_t b = 0; b + 2 < cx.size(); b += 3)
-            jobs.insert(jobs.end(), {(int)gi, cx[b], cy[a], cx[b + 1], cx[b + 2], cy[a + 1], cy[a + 2]});
+          for (size_t b = 0; b + 2 < cx.size(); b += 3) {
+            // strips of the tile inside the grid (the rest would idle)
+            int wxa = 0, wya = 0;
+            while (wxa < wx && cx[b] + wxa * SW <= g.nx) ++wxa;
+            while (wya < wy && cy[a] + wya * trows <= g.ny) ++wya;
+            jobs.insert(jobs.end(), {(int)gi, cx[b], cy[a], cx[b + 1], cx[b + 2], cy[a + 1], cy[a + 2], 0, wxa, wya, 0});
+          }
       }
       kp.tile_wx = wx;
       kp.tile_rows = trows;
     }
   }
-  const int njobs = (int)(jobs.size() / (mode == MODE_BANDS ? 5 : 7));
-  // TILES: give each CTA a contiguous list of jobs, balanced by cost (cells of
-  // the tile's active strips), largest first onto the least-loaded CTA
-  std::vector<int> job_off;
-  if (mode == MODE_TILES) {
-    const int wx = r.cfg.tile_wx, wy = kWarps / wx;
-    std::vector<std::pair<long, int>> cost(njobs);
-    for (int j = 0; j < njobs; ++j) {
-      const int *t = &jobs[7 * (size_t)j];
-      const GridDesc &g = grids[t[0]];
-      long c = 0;
-      for (int b = 0; b < wy; ++b) {
-        const int y0 = t[2] + b * rmax;
-        if (y0 > g.ny) continue;
-        const int rows = std::min(rmax, g.ny + 1 - y0);
-        for (int a = 0; a < wx; ++a)
-          if (t[1] + a * SW <= g.nx) c += (long)rows * SW;
+  const int njobs = (int)(jobs.size() / (mode == MODE_BANDS ? 5 : kTileInts));
+  // TILES: tiles are packed into groups of at most 16 strips that one CTA runs
+  // side by side (a tile keeps only its strips inside the grid, so the small
+  // tiles of a batch share CTAs instead of leaving warps idle): largest tiles
+  // first, each into the fullest group it fits (best fit).  Groups go to CTAs
+  // largest cost (cells) first onto the least-loaded CTA; CTA b runs the
+  // tiles [job_off[b], job_off[b+1]), a group's tiles consecutive.
+  if (mode == MODE_TILES && !tiles_cached) {
+    std::vector<int> order(njobs);
+    for (int j = 0; j < njobs; ++j) order[j] = j;
+    auto warps_of = [&](int j) { return jobs[(size_t)kTileInts * j + 8] * jobs[(size_t)kTileInts * j + 9]; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return warps_of(x) > warps_of(y); });
+    std::vector<std::vector<int>> members;       // tiles of each group
+    std::vector<int> used;                       // warps used by each group
+    std::vector<std::vector<int>> by_free(kWarps + 1);  // groups by free warps
+    for (int j : order) {
+      const int n = warps_of(j);
+      int gsel = -1;
+      for (int f = n; f <= kWarps && gsel < 0; ++f)
+        if (!by_free[f].empty()) {
+          gsel = by_free[f].back();
+          by_free[f].pop_back();
+        }
+      if (gsel < 0) {
+        gsel = (int)members.size();
+        members.emplace_back();
+        used.push_back(0);
       }
-      cost[j] = {c, j};
+      jobs[(size_t)kTileInts * j + 7] = used[gsel];
+      used[gsel] += n;
+      members[gsel].push_back(j);
+      by_free[kWarps - used[gsel]].push_back(gsel);
+    }
+    const int ngroups = (int)members.size();
+    std::vector<std::pair<long, int>> cost(ngroups);
+    for (int gi = 0; gi < ngroups; ++gi) {
+      long c = 0;
+      for (int j : members[gi]) {
+        const int *t = &jobs[(size_t)kTileInts * j];
+        const GridDesc &g = grids[t[0]];
+        for (int b = 0; b < t[9]; ++b) {
+          const int rows = std::min(rmax, g.ny + 1 - (t[2] + b * rmax));
+          c += (long)rows * SW * t[8];
+        }
+      }
+      cost[gi] = {c, gi};
     }
     std::stable_sort(cost.begin(), cost.end(), [](const std::pair<long, int> &x, const std::pair<long, int> &y) {
       return x.first > y.first;
     });
-    std::vector<long> load(ctas, 0);
+    // least-loaded CTA first (ties: lowest index), from a heap
     std::vector<std::vector<int>> lists(ctas);
-    for (const auto &cj : cost) {
-      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      load[b] += cj.first;
-      lists[b].push_back(cj.second);
+    std::priority_queue<std::pair<long, int>, std::vector<std::pair<long, int>>, std::greater<std::pair<long, int>>> heap;
+    for (int b = 0; b < ctas; ++b) heap.push({0L, b});
+    for (const auto &cg : cost) {
+      auto top = heap.top();
+      heap.pop();
+      lists[top.second].push_back(cg.second);
+      heap.push({top.first + cg.first, top.second});
     }
     std::vector<int> reordered;
     reordered.reserve(jobs.size());
     job_off.push_back(0);
     for (int b = 0; b < ctas; ++b) {
-      for (int j : lists[b]) reordered.insert(reordered.end(), &jobs[7 * (size_t)j], &jobs[7 * (size_t)j] + 7);
-      job_off.push_back((int)(reordered.size() / 7));
+      for (int gi : lists[b]) {
+        const size_t first = reordered.size();
+        for (int j : members[gi])
+          reordered.insert(reordered.end(), &jobs[(size_t)kTileInts * j], &jobs[(size_t)kTileInts * j] + kTileInts);
+        reordered[first + 10] = (int)members[gi].size();
+      }
+      job_off.push_back((int)(reordered.size() / kTileInts));
     }
     jobs.swap(reordered);
+    S.tiles_key = tkey;
+    S.tiles_jobs = jobs;
+    S.tiles_off = job_off;
   }
 
   // descriptors: grids, tensor maps, jobs

@@ -46,6 +46,10 @@ struct DtbState {
   void *desc = nullptr;     // grid descriptors, tensor maps, job lists
   size_t desc_bytes = 0;
   std::vector<char> last_desc;  // host copy of what `desc` holds
+  // TILES job lists of the last run, reused while their key (CTAs, tile
+  // shape, rows, depth, grid sizes) is unchanged
+  std::vector<long> tiles_key;
+  std::vector<int> tiles_jobs, tiles_off;
 };
 
 // Largest rows per warp strip that fit in shared memory.
