@@ -30,7 +30,10 @@
 //             with a k-row overlapped halo above and below, k steps per visit;
 //   TILES     independent CTA tiles with a k-deep overlapped halo on all sides
 //             (no cross-CTA exchange at all), k steps per visit; also carries
-//             batches of grids.
+//             batches of grids, partial tiles packed side by side in a CTA.
+// In RESIDENT and BANDS a CTA holds a block of 4 x 4 strips, so that most
+// neighbours share its shared memory.  FP32 TILES strips take two steps per
+// exchange (run_strip_pair), reading their neighbours' cells in place.
 // Every wait is bounded by a %globaltimer deadline; on expiry the kernel
 // records J2D_ERR_TIMEOUT, stops waiting and runs to completion.
 #include <cuda.h>
@@ -78,7 +81,7 @@ struct KParams {
   int rmax, rp;             // strip rows (max), mailbox column length
   int m;                    // BANDS: strips per column (per-wave value in the job)
   int bx;                   // BANDS: CTA block of bx x (16/bx) strips, 0 = 16 strips down a column
-  int tile_wx, tile_rows;   // TILES
+  int tile_rows;            // TILES: rows per strip (tile shapes are per job)
   int *status;
   int *barrier;             // grid barrier counter
   int *gflags;              // per slot step counters (cross-CTA consumers)
@@ -1366,7 +1369,6 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
             jobs.insert(jobs.end(), {(int)gi, cx[b], cy[a], cx[b + 1], cx[b + 2], cy[a + 1], cy[a + 2], 0, wxa, wya, 0});
           }
       }
-      kp.tile_wx = wx;
       kp.tile_rows = trows;
     }
   }
