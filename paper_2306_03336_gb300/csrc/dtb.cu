@@ -32,9 +32,9 @@
 //             (no cross-CTA exchange at all), k steps per visit; also carries
 //             batches of grids, partial tiles packed side by side in a CTA.
 // In RESIDENT and BANDS a CTA holds a block of strips (4 x 4 where the grid
-// allows; see choose_bx), so that most
-// neighbours share its shared memory.  FP32 TILES strips take two steps per
-// exchange (run_strip_pair), reading their neighbours' cells in place.
+// allows; see choose_bx), so that most neighbours share its shared memory.
+// FP32 TILES strips take two steps per exchange (run_strip_pair), reading
+// their neighbours' cells in place.
 // Every wait is bounded by a %globaltimer deadline; on expiry the kernel
 // records J2D_ERR_TIMEOUT, stops waiting and runs to completion.
 #include <cuda.h>
