@@ -64,15 +64,19 @@ __device__ __forceinline__ T stencil(const Links<T> &a, T xm, T xp, T ym, T c, T
 //
 // Fast path: all five weights and values positive normal, exponent spread of
 // the five products at most kExactGuard bits, normal result; otherwise the
-// cell takes the FMA chain.  Exactness: a product of two 53-bit significands
-// has at most 106 bits; shifted into a 128-bit frame with kExactGuard bits of
-// headroom below, five of them sum without loss (< 5 * 2^124 < 2^127), so the
-// frame holds the exact sum and one rounding gives the correctly rounded value.
+// cell takes the FMA chain.  Exactness: each value's 53-bit significand is
+// shifted left by its product's place in the frame, s <= kExactGuard = 11
+// bits (so it still fits 64 bits), and multiplied by the weight's 53-bit
+// significand: each term has at most 117 bits, five of them sum without loss
+// in a 128-bit frame (< 5 * 2^117 < 2^120), so the frame holds the exact sum
+// and one rounding gives the correctly rounded value.  (A guard of 11 rather
+// than a wider one saves two shifts per term, the value being shifted before
+// the multiply instead of the 106-bit product after it.)
 // bit (y & 3) * 2 + (x & 1) set: cell (x, y) takes the integer path.  Rows
 // with y mod 4 in {0, 1}: half of the cells, the pattern that measured fastest
 // across the resident, tiles and one-step kernels.
 constexpr unsigned kExactMask = 0x0F;
-constexpr int kExactGuard = 18;
+constexpr int kExactGuard = 11;
 
 struct ExactW {
   uint64_t m[5];  // significands with the implicit bit, order xm, xp, ym, c, yp
@@ -107,7 +111,8 @@ __device__ __forceinline__ void add128(uint32_t (&a)[4], uint32_t b0, uint32_t b
 // Correctly rounded xm*W + xp*E + ym*S + c*C + yp*N on the fast path; returns
 // false (r untouched) when the fast path does not apply.  Significands are
 // split into 32-bit words (high word 21 bits with the implicit bit); a
-// product is four 32x32->64 multiplies; the frame is four 32-bit words.
+// product of the shifted value significand (two words) and the weight
+// significand is four 32x32->64 multiplies; the frame is four 32-bit words.
 __device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double xp, double ym, double c, double yp,
                                               double &r) {
   const double v[5] = {xm, xp, ym, c, yp};
@@ -130,17 +135,17 @@ __device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double
   for (int i = 0; i < 5; ++i) {
     const int s = kExactGuard - (Em - E[i]);  // frame position: p_i * 2^s, s <= kExactGuard
     sall |= s;                               // any s < 0 leaves the fast path
+    const uint32_t a0 = m0[i] << (s & 31), a1 = __funnelshift_l(m0[i], m1[i], s);  // value significand * 2^s
     const uint32_t b0 = (uint32_t)u.m[i], b1 = (uint32_t)(u.m[i] >> 32);
-    const uint64_t p00 = (uint64_t)m0[i] * b0;
-    const uint64_t p01 = (uint64_t)m0[i] * b1 + (p00 >> 32);
-    const uint64_t p10 = (uint64_t)m1[i] * b0 + (uint32_t)p01;
-    const uint64_t p11 = (uint64_t)m1[i] * b1 + (p01 >> 32) + (p10 >> 32);
-    const uint32_t w0 = (uint32_t)p00, w1 = (uint32_t)p10, w2 = (uint32_t)p11, w3 = (uint32_t)(p11 >> 32);
-    add128(f, w0 << (s & 31), __funnelshift_l(w0, w1, s), __funnelshift_l(w1, w2, s), __funnelshift_l(w2, w3, s));
+    const uint64_t p00 = (uint64_t)a0 * b0;
+    const uint64_t p01 = (uint64_t)a0 * b1 + (p00 >> 32);
+    const uint64_t p10 = (uint64_t)a1 * b0 + (uint32_t)p01;
+    const uint64_t p11 = (uint64_t)a1 * b1 + (p01 >> 32) + (p10 >> 32);
+    add128(f, (uint32_t)p00, (uint32_t)p10, (uint32_t)p11, (uint32_t)(p11 >> 32));
   }
   ok &= sall >= 0;
-  // frame F = f[3]:f[2]:f[1]:f[0] = sum * 2^(2150 + kExactGuard - Em), F in [2^122, 2^127)
-  const int z = __clz((int)f[3]) & 31;  // 1..5 on the fast path
+  // frame F = f[3]:f[2]:f[1]:f[0] = sum * 2^(2150 + kExactGuard - Em), F in [2^115, 2^120)
+  const int z = __clz((int)f[3]) & 31;  // 8..12 on the fast path
   const uint32_t g3 = __funnelshift_l(f[2], f[3], z), g2 = __funnelshift_l(f[1], f[2], z);
   const uint32_t g1 = __funnelshift_l(f[0], f[1], z), g0 = f[0] << z;
   uint64_t kept = ((uint64_t)g3 << 21) | (g2 >> 11);  // the top 53 bits

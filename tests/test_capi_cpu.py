@@ -75,9 +75,9 @@ def test_arith_info_without_gpu(lib):
     the cells (rows with y mod 4 in {0, 1}) on the integer path, 18 guard bits."""
     m, g = ctypes.c_uint(), ctypes.c_int()
     assert lib.j2d5pt_arith_info(ctypes.byref(m), ctypes.byref(g)) == j2d5pt.J2D_OK
-    assert m.value == 0x0F and g.value == 18
+    assert m.value == 0x0F and g.value == 11
     assert lib.j2d5pt_arith_info(None, None) == j2d5pt.J2D_OK
-    assert j2d5pt.j2d5pt_arith_info() == (0x0F, 18)
+    assert j2d5pt.j2d5pt_arith_info() == (0x0F, 11)
 
 
 def test_plan_without_gpu_reports_device_error(lib):
