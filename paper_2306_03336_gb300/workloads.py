@@ -4,6 +4,7 @@
   python -m paper_2306_03336_gb300.workloads f32tiles   # FP32 8192^2, tiles k=16, 16 steps (one launch)
   python -m paper_2306_03336_gb300.workloads f32onestep # FP32 8192^2, one-step kernel, 4 steps
   python -m paper_2306_03336_gb300.workloads f64onestep # FP64 2048x1536, one-step kernel, 8 steps
+  python -m paper_2306_03336_gb300.workloads f64tiles   # FP64 8192^2, tiles k=4, 4 strips wide, 8 steps (one launch)
 
 Inputs are the seeded synthetic fields of paper_2306_03336_gb300.synth.
 """
@@ -44,6 +45,11 @@ def main(which):
     elif which == "f32onestep":
         p, src, dst = _plan(8192, 8192, "f32", "onestep")
         p.run(src, dst, 4)
+        p.sync()
+        p.close()
+    elif which == "f64tiles":
+        p, src, dst = _plan(8192, 8192, "f64", "tiles", 4, 4)
+        p.run(src, dst, 8)
         p.sync()
         p.close()
     elif which == "f64onestep":
