@@ -1,14 +1,16 @@
 """Benchmark: j2d5pt on one GB300, GCells/s (interior cell updates per second).
 
-Headline workload (one line of JSON): FP64, 2048 x 1536 interior cells plus
+Headline workload (one line of JSON): FP64, 16384 x 16384 interior cells plus
 the one-cell ring, seeded uniform [0,1) data and normalised weights, 1000 time
 steps per benchmark step (one benchmark step = one j2d5pt_run of 1000 time
 steps).  The plan is autotuned first (one-step / resident / bands / tiles over
-temporal depths), then timed.  The other workloads (FP64 and FP32 16384^2 with
-1000 steps, 256 batched grids with 200 steps, the 4096^2 gradient with 500
-steps) are reported under "extras", each against the one-step kernel.
+temporal depths and tile shapes), then timed.  The other workloads (FP64
+2048 x 1536, FP32 16384^2, the paper's 8592 x 8328 domain, 256 batched grids,
+the 4096^2 gradient) are reported under "extras", each with the one-step
+kernel beside it and its own roofline record (median of 3 repetitions).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload NAME   # one named run for profiling (see WORKLOADS)
 
 Timing: CUDA events on the launching stream; L2 flushed (256 MiB write)
 between benchmark steps; synchronise before and after.  The roofline uses the
@@ -32,17 +34,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GCells/s (cell-updates/s) at 1 GB300, FP64 and FP32, and % of roofline vs 1-step kernel"
-WORKLOAD = "j2d5pt_f64_2048x1536_1000"
+WORKLOAD = "j2d5pt_f64_16384x16384_1000"
+HEAD_N, HEAD_T = 16384, 1000
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)  # ~1 s timed: several clock samples
+    ap.add_argument("--steps", type=int, default=12)  # ~20 s timed at 1.65 s per step
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default=None, help="run one named workload once (profiling) and exit")
     return ap.parse_args()
 
 
@@ -170,6 +174,81 @@ def aggregate(total_ms, cells_per_rank, world, device="cuda"):
     return total_ms, cells_per_rank * world / (total_ms * 1e-3) / 1e9
 
 
+# ---- peaks and roofline records ---------------------------------------------
+
+def measure_peaks(j2d5pt):
+    """Roofline denominators measured live on this GPU (and the driver's HBM copy figure)."""
+    fma64 = j2d5pt.j2d5pt_measure_fma_rate(j2d5pt.J2D_F64)
+    fma32 = j2d5pt.j2d5pt_measure_fma_rate(j2d5pt.J2D_F32)
+    exact = j2d5pt.j2d5pt_measure_exact_rate()
+    smem = j2d5pt.j2d5pt_measure_smem_bandwidth()
+    mask, _ = j2d5pt.j2d5pt_arith_info()
+    f = bin(mask & 0xFF).count("1") / 8.0
+    # FP64 cell rate: half of the cells (the exact mask) run on the integer
+    # pipes, the rest as 5 FP64 FMA instructions; the two pipes work in
+    # parallel, so the peak is set by the slower share, each at its measured rate
+    chain = fma64 / 5
+    alu = 1.0 / max((1.0 - f) / chain, f / exact if f else 0.0)
+    hbm = None
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] * 1e9
+    except Exception:
+        pass
+    return {"fma64": fma64, "fma32": fma32, "exact": exact, "smem": smem, "share": f, "alu_cells": alu,
+            "hbm": hbm}
+
+
+def roof_f64(pk, kernel_gcells, traffic=None, kernel="dtb_kernel"):
+    """FP64: arithmetic bound (FP64 pipe plus the integer path), 9 flops per cell update."""
+    achieved = kernel_gcells * 9 / 1e3
+    peak = pk["alu_cells"] / 1e9 * 9 / 1e3
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel,
+            "peak_source": ("of measured: FP64 pipe %.1f GFMA/s (j2d5pt_measure_fma_rate) / 5 per chain cell, "
+                            "integer path %.1f Gcells/s (j2d5pt_measure_exact_rate), exact share %.3f; x 9 flops "
+                            "per cell" % (pk["fma64"] / 1e9, pk["exact"] / 1e9, pk["share"])),
+            "kernel_gcells": round(kernel_gcells, 3), "peak_gcells": round(pk["alu_cells"] / 1e9, 3),
+            "fp64_pipe_only_gcells": round(pk["fma64"] / 5 / 1e9, 3)}
+
+
+def roof_f32_dtb(pk, kernel_gcells, sweep):
+    """FP32 blocked kernels: on chip.  Shared memory carries one 4-byte load
+    and store per cell per sweep (a sweep advances `sweep` steps); the FP32
+    pipe does 5 FMA instructions per cell update.  The bound reported is the
+    shared-memory pipe (the busiest unit in the profile); the FP32-pipe
+    fraction is given beside it."""
+    bpc = 8.0 / sweep
+    achieved = kernel_gcells * 1e9 * bpc / 1e9
+    peak = pk["smem"] / 1e9
+    return {"bound": "smem", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "bytes_per_cell_update": bpc,
+            "frac_fp32_pipe": round(kernel_gcells * 1e9 * 5 / pk["fma32"], 4),
+            "peak_source": "of measured: shared memory j2d5pt_measure_smem_bandwidth; FP32 FMA j2d5pt_measure_fma_rate",
+            "kernel_gcells": round(kernel_gcells, 3)}
+
+
+def roof_hbm(pk, kernel_gcells, elem):
+    """One-step kernel, HBM: one read and one write of the element per cell update."""
+    if not pk["hbm"]:
+        return None
+    achieved = kernel_gcells * 2 * elem
+    peak = pk["hbm"] / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
+            "kernel_gcells": round(kernel_gcells, 3)}
+
+
+def reps(plan, fn, flush, stream, cells, n=3):
+    """Median over n repetitions (after one warm-up) of the whole-call and kernel GCells/s."""
+    total, kern = timed(plan, fn, n, 1, flush, stream)
+    out = {"gcells": round(gcells(cells, statistics.median(total)), 2), "reps": n}
+    if kern and kern[0] is not None:
+        out["kernel_gcells"] = round(gcells(cells, statistics.median(kern)), 2)
+    return out
+
+
+# ---- the headline -----------------------------------------------------------
+
 def run_ours(args):
     import torch
     import __graft_entry__
@@ -182,7 +261,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     flush = L2Flush()
-    nx, ny, steps_t = 2048, 1536, 1000
+    nx = ny = HEAD_N
+    steps_t = HEAD_T
     u0 = synth.field(nx, ny, synth.data_seed(1))
     w = synth.weights(synth.weight_seed(1))
     plan = j2d5pt.Plan(nx, ny, "f64", w)
@@ -210,43 +290,32 @@ def run_ours(args):
     cells = nx * ny * steps_t
     total_ms, value = aggregate(sum(total), cells * args.steps, world)
 
-    # roofline of the dominant kernel: arithmetic.  An FP64 cell update is 9
-    # flops (5 multiplies, 4 adds).  Half the cells (the exact mask) run on
-    # the integer pipes, the rest as 5 FP64 FMA instructions on the FP64 pipe;
-    # the two pipes work in parallel, so the peak cell rate is set by the
-    # slower of the two shares, each at its measured rate.
-    fma64 = j2d5pt.j2d5pt_measure_fma_rate(j2d5pt.J2D_F64)
-    alu = alu_peak(j2d5pt, fma64)
+    pk = measure_peaks(j2d5pt)
     kern_ms = statistics.mean(kern)
-    achieved = cells * 9 / (kern_ms * 1e-3) / 1e12
-    peak = alu["peak_gcells"] * 9 / 1e3
-    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic_for("f64_2048x1536_1000_" + algo),
-            "kernel": "dtb_kernel" if algo != "onestep" else "onestep_kernel",
-            "peak_source": ("measured: FP64 pipe %.1f GFMA/s (j2d5pt_measure_fma_rate) / 5 per chain cell, integer "
-                            "path %.1f Gcells/s (j2d5pt_measure_exact_rate), exact share %.3f; x 9 flops per cell"
-                            % (fma64 / 1e9, alu["exact_gcells"], alu["exact_share"])),
-            "kernel_gcells": round(gcells(cells, kern_ms), 3), "peak_gcells": alu["peak_gcells"],
-            "fp64_pipe_only_gcells": round(fma64 / 5 / 1e9, 3)}
+    roof = roof_f64(pk, gcells(cells, kern_ms), traffic_for("f64_16384x16384_1000_" + algo),
+                    "dtb_kernel" if algo != "onestep" else "onestep_kernel")
 
     # end to end through the C ABI on host buffers (pinned input and output)
     host_in = torch.from_numpy(u0).pin_memory().numpy()
     host_out = torch.empty(u0.shape, dtype=torch.float64).pin_memory().numpy()
     t_e2e = []
-    for i in range(args.warmup + args.steps):
+    n_e2e = max(3, min(args.steps, 5))
+    for i in range(1 + n_e2e):
         flush()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out_h = plan.run_host(host_in, steps_t, out=host_out)
         t1 = time.perf_counter()
-        if i >= args.warmup:
+        if i >= 1:
             t_e2e.append(t1 - t0)
     e2e = {"value": round(cells * len(t_e2e) * world / sum(t_e2e) / 1e9, 3), "unit": "GCells/s",
-           "h2d_bytes_per_step": int(host_in.nbytes), "d2h_bytes_per_step": int(out_h.nbytes)}
+           "h2d_bytes_per_step": int(host_in.nbytes), "d2h_bytes_per_step": int(out_h.nbytes),
+           "reps": len(t_e2e)}
+    del host_in, host_out
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu["peak_gcells"])
+        extras = run_extras(j2d5pt, synth, flush, stream, pk, plan, src, dst)
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(u0, w)
@@ -257,7 +326,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded uniform [0,1) field and normalised uniform weights)",
             "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "time_steps": steps_t, "plan": plan.describe(),
-                       "l2": "flushed (256 MiB write) between steps",
+                       "l2": "inputs (2.15 GB per buffer) larger than L2, and L2 flushed (256 MiB write) between steps",
                        "parallelism": "replicas (single-GPU method)" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches_per_step * args.steps), "clocks": clk, "extras": extras,
@@ -268,120 +337,147 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def alu_peak(j2d5pt, fma64):
-    """Arithmetic peak of the FP64 kernels in cells/s (see run_ours)."""
-    exact = j2d5pt.j2d5pt_measure_exact_rate()
-    mask, _ = j2d5pt.j2d5pt_arith_info()
-    f = bin(mask & 0xFF).count("1") / 8.0
-    chain = fma64 / 5
-    peak = 1.0 / max((1.0 - f) / chain, f / exact if f else 0.0)
-    return {"peak_gcells": round(peak / 1e9, 3), "exact_gcells": round(exact / 1e9, 3), "exact_share": f}
+def oracle_blocks_err(u0_f64, w, steps, got_view, size=256):
+    """Max relative error of a GPU result against the FP64 oracle on blocks
+    (corners, middle) evaluated exactly on windows of radius steps+1."""
+    import oracle
+    oracle.build()
+    H, W = u0_f64.shape
+    blocks = [(0, size, 0, size), ((H - size) // 2, (H + size) // 2, (W - size) // 2, (W + size) // 2),
+              (H - size, H, W - size, W)]
+    worst = 0.0
+    for (y0, y1, x0, x1) in blocks:
+        r = steps + 1
+        a0, a1, b0, b1 = max(0, y0 - r), min(H, y1 + r), max(0, x0 - r), min(W, x1 + r)
+        ref = oracle.run(np.ascontiguousarray(u0_f64[a0:a1, b0:b1]), w, steps, threads=oracle.max_threads())
+        ref = ref[y0 - a0:y1 - a0, x0 - b0:x1 - b0]
+        got = got_view[y0:y1, x0:x1].double().cpu().numpy()
+        worst = max(worst, float((np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)).max()))
+    return worst, "FP64 oracle on %d blocks of %dx%d cells (corners, middle), exact windows of radius %d" % (
+        len(blocks), size, size, steps + 1)
 
 
-def one(plan, fn, flush, stream, cells, reps=1):
-    total, kern = timed(plan, fn, reps, 1, flush, stream)
-    return round(gcells(cells, min(total)), 2), round(gcells(cells, min(kern)), 2)
+def same_choice(p, desc):
+    """Give plan p the algorithm, depth and tile shape another plan's description names."""
+    f = dict(kv.split("=") for kv in desc.split())
+    p.set("algo", f["algo"])
+    if f["algo"] not in ("resident", "onestep"):
+        p.set("depth", int(f["depth"])).set("tile_wx", int(f["tile_wx"]))
+    return p
 
 
-def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
-    """Secondary workloads, each beside the one-step kernel."""
+def run_extras(j2d5pt, synth, flush, stream, pk, head_plan, head_src, head_dst):
+    """Secondary workloads, each beside the one-step kernel, each with its roofline record."""
     import torch
-    out = {}
-    hbm = None
-    try:
-        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except Exception:
-        pass
-    fma32 = j2d5pt.j2d5pt_measure_fma_rate(j2d5pt.J2D_F32)
-    smem = j2d5pt.j2d5pt_measure_smem_bandwidth() / 1e9  # GB/s
-    out["peaks"] = {"fp64_gfma_s": round(fma64 / 1e9, 1), "fp32_gfma_s": round(fma32 / 1e9, 1), "hbm_gbs": hbm,
-                    "fp64_alu_gcells": alu64, "smem_gbs": round(smem, 1)}
-    # DTB shared-memory traffic per cell update: one read and one write of the
-    # element (the in-place row sweep); frac_smem = that rate / measured peak
+    out = {"peaks": {"fp64_gfma_s": round(pk["fma64"] / 1e9, 1), "fp32_gfma_s": round(pk["fma32"] / 1e9, 1),
+                     "hbm_gbs": round(pk["hbm"] / 1e9, 1) if pk["hbm"] else None,
+                     "fp64_alu_gcells": round(pk["alu_cells"] / 1e9, 2), "exact_gcells": round(pk["exact"] / 1e9, 2),
+                     "smem_gbs": round(pk["smem"] / 1e9, 1)}}
+    w = head_plan.weights[0]
 
-    # 1) the headline grid through each kernel family
+    # 1) the headline grid (16384^2 FP64): one-step kernel, the FMA chain alone
+    n, T = HEAD_N, HEAD_T
+    cells = n * n * T
+    p = j2d5pt.Plan(n, n, "f64", w).set("algo", "onestep").set("timing", 1)
+    r = reps(p, lambda: p.run(head_src, head_dst, T, stream), flush, stream, cells)
+    r["roofline"] = roof_f64(pk, r["kernel_gcells"], kernel="onestep_kernel")
+    p.close()
+    ent = {"onestep": r}
+    p = same_choice(j2d5pt.Plan(n, n, "f64", w), head_plan.describe()).set("timing", 1).set("int_path", 0)
+    r = reps(p, lambda: p.run(head_src, head_dst, T, stream), flush, stream, cells)
+    r["frac_fp64_pipe"] = round(r["kernel_gcells"] / (pk["fma64"] / 5 / 1e9), 4)
+    r["plan"] = p.describe()
+    p.close()
+    ent["fma_chain_only"] = r
+    out["f64_16384x16384_1000"] = ent
+
+    # 2) FP64 2048 x 1536, 1000 steps (fits on chip): every kernel family
     nx, ny, T = 2048, 1536, 1000
+    u0 = synth.field(nx, ny, synth.data_seed(1))
+    w1 = synth.weights(synth.weight_seed(1))
+    cells = nx * ny * T
     fam = {}
+    pa = j2d5pt.Plan(nx, ny, "f64", w1)
+    a, b = pa.to_device(u0), pa.empty()
+    pa.autotune(a, b, T)
+    pa.set("timing", 1)
+    r = reps(pa, lambda: pa.run(a, b, T, stream), flush, stream, cells)
+    r["roofline"] = roof_f64(pk, r["kernel_gcells"])
+    r["plan"] = pa.describe()
+    fam["autotuned"] = r
+    pa.close()
     for algo, depth in (("onestep", 0), ("resident", 0), ("bands", 16), ("tiles", 8)):
-        p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", algo).set("timing", 1)
+        p = j2d5pt.Plan(nx, ny, "f64", w1).set("algo", algo).set("timing", 1)
         if depth:
             p.set("depth", depth)
-        run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)
-        fam[algo] = {"gcells": run, "kernel_gcells": kern, "frac_alu": round(kern / alu64, 3)}
-        if algo != "onestep":
-            fam[algo]["frac_smem"] = round(kern * 16 / smem, 3)
+        r = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
+        r["frac_alu"] = round(r["kernel_gcells"] * 1e9 / pk["alu_cells"], 4)
+        fam[algo] = r
         p.close()
-    # the one-step baseline with its 1000 launches replayed from a CUDA graph
-    p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", "onestep").set("graph", 1)
-    p.run(src, dst, T, stream)
-    total, _ = timed(p, lambda: p.run(src, dst, T, stream), 1, 1, flush, stream)
-    run = round(gcells(nx * ny * T, min(total)), 2)
-    fam["onestep_graph"] = {"gcells": run, "frac_alu": round(run / alu64, 3)}
+    p = j2d5pt.Plan(nx, ny, "f64", w1).set("algo", "onestep").set("graph", 1)
+    p.run(a, b, T, stream)
+    r = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
+    r["frac_alu"] = round(r["gcells"] * 1e9 / pk["alu_cells"], 4)
+    fam["onestep_graph"] = r
     p.close()
-    # the same resident kernel with every cell on the FMA chain (integer path off)
-    p = j2d5pt.Plan(nx, ny, "f64", w).set("algo", "resident").set("timing", 1).set("int_path", 0)
-    run, kern = one(p, lambda: p.run(src, dst, T, stream), flush, stream, nx * ny * T)
-    fam["resident_fma_chain_only"] = {"gcells": run, "kernel_gcells": kern,
-                                      "frac_fp64_pipe": round(kern / (fma64 / 5 / 1e9), 3)}
+    p = j2d5pt.Plan(nx, ny, "f64", w1).set("algo", "resident").set("timing", 1).set("int_path", 0)
+    r = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
+    r["frac_fp64_pipe"] = round(r["kernel_gcells"] / (pk["fma64"] / 5 / 1e9), 4)
+    fam["resident_fma_chain_only"] = r
     p.close()
     out["f64_2048x1536_1000"] = fam
+    del a, b
 
-    # 2) 16384^2, FP64 and FP32 from the same seeded data, 1000 steps
-    n, T = 16384, 1000
+    # 3) FP32 16384^2, 1000 steps, same seeded data as the headline; error
+    #    against the FP64 oracle (exact windows around blocks of cells)
+    n, T = HEAD_N, HEAD_T
+    cells = n * n * T
     u0 = synth.field(n, n, synth.data_seed(1))
-    res = {}
-    for dt in ("f64", "f32"):
-        p = j2d5pt.Plan(n, n, dt, w)
-        a = p.to_device(u0 if dt == "f64" else u0.astype(np.float32))
-        b = p.empty()
-        p.set("algo", "onestep").set("timing", 1)
-        r1, k1 = one(p, lambda: p.run(a, b, T, stream), flush, stream, n * n * T)
-        p.autotune(a, b, T)
-        best = p.describe()
-        r2, k2 = one(p, lambda: p.run(a, b, T, stream), flush, stream, n * n * T)
-        ent = {"onestep_gcells": r1, "best_gcells": r2, "best_kernel_gcells": k2, "best_plan": best}
-        if dt == "f64":
-            ent["onestep_frac_alu"] = round(k1 / alu64, 3)
-            ent["best_frac_alu"] = round(k2 / alu64, 3)
-            ent["best_frac_smem"] = round(k2 * 16 / smem, 3)
-            ref64 = p.view(b).clone()
-        else:
-            if hbm:
-                ent["onestep_frac_hbm"] = round(k1 * 8 / hbm, 3)
-            ent["best_frac_fp32_pipe"] = round(k2 / (fma32 / 5 / 1e9), 3)
-            # one 4-byte load and store per cell per sweep; a sweep advances `sweep` steps
-            sweep = int(dict(kv.split("=") for kv in best.split()).get("sweep", "1"))
-            ent["best_frac_smem"] = round(k2 * 8 / sweep / smem, 3)
-            got = p.view(b).double()
-            ent["max_rel_err_vs_fp64"] = float(((got - ref64).abs().max() / ref64.abs().max()).item())
-            del ref64
-        res[dt] = ent
-        del a, b
-        p.close()
-        torch.cuda.empty_cache()
-    out["16384x16384_1000"] = res
+    p = j2d5pt.Plan(n, n, "f32", w)
+    a, b = p.to_device(u0.astype(np.float32)), p.empty()
+    p.set("algo", "onestep").set("timing", 1)
+    r1 = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
+    r1["roofline"] = roof_hbm(pk, r1["kernel_gcells"], 4)
+    p.set("algo", "auto")
+    p.autotune(a, b, T)
+    p.set("timing", 1)
+    r2 = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
+    sweep = int(dict(kv.split("=") for kv in p.describe().split()).get("sweep", "1"))
+    r2["roofline"] = roof_f32_dtb(pk, r2["kernel_gcells"], sweep)
+    r2["plan"] = p.describe()
+    err, how = oracle_blocks_err(u0.astype(np.float32).astype(np.float64), w, T, p.view(b))
+    out["f32_16384x16384_1000"] = {"onestep": r1, "autotuned": r2, "max_rel_err_vs_fp64_oracle": err,
+                                   "error_sample": how}
+    p.close()
+    del a, b
+    torch.cuda.empty_cache()
 
-    # 2b) the paper's evaluation domain (Figure 2): 8592 x 8328 run, 8192^2 counted
-    #     as the valid domain ("pruned"), FP64 and FP32, 1000 steps, autotuned
+    # 4) the paper's evaluation domain (Section 4, Figure 2): 8592 x 8328 run,
+    #    8192^2 counted as the valid domain ("pruned"), FP64 and FP32, autotuned
     pd = {}
+    nx_, ny_ = 8592, 8328
+    uu = synth.field(nx_, ny_, synth.data_seed(1) + 20)
     for dt in ("f64", "f32"):
-        nx_, ny_ = 8592, 8328
         p = j2d5pt.Plan(nx_, ny_, dt, w)
-        uu = synth.field(nx_, ny_, synth.data_seed(1) + 20)
         a = p.to_device(uu if dt == "f64" else uu.astype(np.float32))
         b = p.empty()
         p.autotune(a, b, 1000)
         p.set("timing", 1)
-        total, kern = timed(p, lambda: p.run(a, b, 1000, stream), 1, 1, flush, stream)
-        t = min(total)
-        pd[dt] = {"gcells_full_domain": round(gcells(nx_ * ny_ * 1000, t), 2),
-                  "gcells_valid_8192sq": round(gcells(8192 * 8192 * 1000, t), 2), "plan": p.describe()}
+        r = reps(p, lambda: p.run(a, b, 1000, stream), flush, stream, nx_ * ny_ * 1000)
+        r["gcells_valid_8192sq"] = round(r["gcells"] * 8192 * 8192 / (nx_ * ny_), 2)
+        if dt == "f64":
+            r["roofline"] = roof_f64(pk, r["kernel_gcells"])
+        else:
+            sw = int(dict(kv.split("=") for kv in p.describe().split()).get("sweep", "1"))
+            r["roofline"] = roof_f32_dtb(pk, r["kernel_gcells"], sw)
+        r["plan"] = p.describe()
+        pd[dt] = r
         p.close()
         del a, b
         torch.cuda.empty_cache()
     out["paper_domain_8592x8328_1000"] = pd
 
-    # 3) 256 batched FP64 grids, sides uniform in [64, 1024], 200 steps, CUDA graph
+    # 5) 256 batched FP64 grids, sides uniform in [64, 1024], 200 steps, CUDA graph
     cfg = synth.WORKLOADS["j2d5pt_f64_batch256_200"]
     sizes = synth.batch_sizes(cfg["count"], synth.data_seed(cfg["index"]), cfg["lo"], cfg["hi"])
     ws = np.stack([synth.weights(synth.weight_seed(cfg["index"]) + i) for i in range(len(sizes))])
@@ -389,15 +485,19 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
     srcs = [p.to_device(synth.field(a_, b_, synth.data_seed(cfg["index"]) + 10 + i), i) for i, (a_, b_) in enumerate(sizes)]
     dsts = [p.empty(i) for i in range(len(sizes))]
     p.autotune_batched(srcs, dsts, cfg["steps"])
-    p.set("graph", 1).set("timing", 1)
+    p.set("graph", 1)
     cells = sum(a_ * b_ for a_, b_ in sizes) * cfg["steps"]
-    rb, kb = one(p, lambda: p.run_batched(srcs, dsts, cfg["steps"], stream), flush, stream, cells, reps=2)
-    out["f64_batch256_200"] = {"gcells": rb, "plan": p.describe(), "cells_per_step": int(cells / cfg["steps"])}
+    p.run_batched(srcs, dsts, cfg["steps"], stream)
+    r = reps(p, lambda: p.run_batched(srcs, dsts, cfg["steps"], stream), flush, stream, cells)
+    r["roofline"] = roof_f64(pk, r["gcells"])
+    r["plan"] = p.describe()
+    r["cells_per_step"] = int(cells / cfg["steps"])
+    out["f64_batch256_200"] = r
     p.close()
     del srcs, dsts
     torch.cuda.empty_cache()
 
-    # 4) gradient of L = <g, u_T>, 4096^2 FP64, 500 steps, checkpoints every 50
+    # 6) gradient of L = <g, u_T>, 4096^2 FP64, 500 steps, checkpoints every 50
     from paper_2306_03336_gb300.autograd import J2D5PT
     cfg = synth.WORKLOADS["j2d5pt_f64_4096x4096_500_adjoint"]
     n, T = cfg["nx"], cfg["steps"]
@@ -405,20 +505,25 @@ def run_extras(j2d5pt, synth, flush, stream, src, dst, w, fma64, alu64):
     ut = torch.tensor(synth.field(n, n, synth.data_seed(cfg["index"])), device="cuda", requires_grad=True)
     wt = torch.tensor(synth.weights(synth.weight_seed(cfg["index"])), device="cuda", requires_grad=True)
     G = torch.tensor(synth.field(n, n, synth.data_seed(cfg["index"]) + 7), device="cuda")
-    for rep in range(2):
+    times = []
+    for rep in range(4):
         ut.grad = None
         wt.grad = None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         (op(ut, wt, T) * G).sum().backward()
         torch.cuda.synchronize()
-        dt_ = time.perf_counter() - t0
+        if rep:
+            times.append(time.perf_counter() - t0)
+    dt_ = statistics.median(times)
     p = j2d5pt.Plan(n, n, "f64", wt.detach().cpu().numpy()).set("timing", 1)
     a, b = p.to_device(G.cpu().numpy()), p.empty()
-    radj, kadj = one(p, lambda: p.run_adjoint(a, b, T, stream), flush, stream, n * n * T)
-    out["f64_4096x4096_500_grad"] = {"fwd_bwd_seconds": round(dt_, 4),
+    ra = reps(p, lambda: p.run_adjoint(a, b, T, stream), flush, stream, n * n * T)
+    ra["roofline"] = roof_f64(pk, ra["kernel_gcells"])
+    ra["plan"] = p.describe()
+    out["f64_4096x4096_500_grad"] = {"fwd_bwd_seconds": round(dt_, 4), "reps": len(times),
                                     "fwd_bwd_gcells": round(n * n * T / dt_ / 1e9, 2),
-                                    "adjoint_only_gcells": radj, "checkpoint": cfg["checkpoint"]}
+                                    "adjoint_only": ra, "checkpoint": cfg["checkpoint"]}
     p.close()
     op.close()
     return out
@@ -449,13 +554,13 @@ def run_reference(args):
     import oracle
     from paper_2306_03336_gb300 import synth
     oracle.build()
-    nx, ny = 2048, 1536
+    nx = ny = HEAD_N
     u0 = synth.field(nx, ny, synth.data_seed(1))
     w = synth.weights(synth.weight_seed(1))
     threads = len(os.sched_getaffinity(0))
-    sample_steps = 200
+    sample_steps = 4
     for _ in range(args.warmup):
-        oracle.run(u0, w, 2, threads=threads)
+        oracle.run(u0, w, 1, threads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.run(u0, w, sample_steps, threads=threads)
@@ -466,16 +571,59 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded uniform [0,1) field and normalised uniform weights)",
-            "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "time_steps": 1000, "sample": sample},
+            "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "time_steps": HEAD_T, "sample": sample},
             "cpu_baseline": {"value": round(value, 4), "unit": "GCells/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GCells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ---- named runs for profiling --------------------------------------------------
+# name: (nx, ny, dtype, algo, depth, tile_wx, steps, runs); algo "auto" = autotuned
+WORKLOADS = {
+    "headline": (HEAD_N, HEAD_N, "f64", "auto", 0, 0, HEAD_T, 2),
+    "f64tiles": (8192, 8192, "f64", "tiles", 4, 4, 8, 1),
+    "f64resident": (2048, 1536, "f64", "resident", 0, 0, 1000, 1),
+    "f64onestep": (2048, 1536, "f64", "onestep", 0, 0, 8, 1),
+    "f32tiles": (8192, 8192, "f32", "tiles", 16, 2, 16, 1),
+    "f32onestep": (8192, 8192, "f32", "onestep", 0, 0, 4, 1),
+}
+
+
+def run_workload(name):
+    """One named workload on the seeded inputs, for ncu; prints the plan and exits."""
+    import torch
+    import __graft_entry__
+    from paper_2306_03336_gb300 import j2d5pt, synth
+    if name not in WORKLOADS:
+        raise SystemExit("unknown workload %r (one of %s)" % (name, ", ".join(sorted(WORKLOADS))))
+    nx, ny, dt, algo, depth, wx, steps, runs = WORKLOADS[name]
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    p = j2d5pt.Plan(nx, ny, dt, synth.weights(synth.weight_seed(1)))
+    u0 = synth.field(nx, ny, synth.data_seed(1))
+    src = p.to_device(u0 if dt == "f64" else u0.astype(np.float32))
+    dst = p.empty()
+    if algo == "auto":
+        p.autotune(src, dst, steps)
+    else:
+        p.set("algo", algo)
+        if depth:
+            p.set("depth", depth)
+        if wx:
+            p.set("tile_wx", wx)
+    for _ in range(runs):
+        p.run(src, dst, steps)
+    p.sync()
+    print(name, p.describe(), flush=True)
+    p.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload:
+        run_workload(args.workload)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

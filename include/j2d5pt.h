@@ -171,7 +171,7 @@ j2d_status j2d5pt_adjoint_step_wgrad(j2d5pt_plan_t plan, const void *u_t, const 
                                      double *dw, void *stream);
 
 /* Same reduction for callers that cannot allocate device memory; no plan
- * needed.  (The paper has no counterpart: this is a deployment variant.)
+ * needed.  The paper has no counterpart to this call.
  * Callers that cannot call cudaMalloc: code running while a stream is being
  * captured into a CUDA graph, code whose device memory is owned by a
  * framework's caching allocator, and latency-bound loops that cannot absorb
@@ -182,8 +182,8 @@ j2d_status j2d5pt_adjoint_step_wgrad(j2d5pt_plan_t plan, const void *u_t, const 
  * (nx, ny, dtype); dw as for j2d5pt_weight_grad (accumulated).  Grids needing
  * more than 65536 partial-sum blocks (about 1.1e9 FP64 or 2.1e9 FP32 cells)
  * are rejected with J2D_ERR_ARG.  The first call on each device looks up the
- * array's device address (once, with that device current); make it before
- * any stream capture.  All calls share the one array: calls that overlap on
+ * array's device address (once, with that device current; again after the
+ * device's context was reset); make it before any stream capture.  All calls share the one array: calls that overlap on
  * the GPU (other streams, other threads) race and give wrong results;
  * serialise them.  Asynchronous on `stream`. */
 j2d_status j2d5pt_weight_grad_noalloc(int nx, int ny, j2d_dtype dtype, const void *u_t,

@@ -118,15 +118,10 @@ static j2d_status plan_common(j2d5pt_plan_t *out, int count, const int *nx, cons
   if ((e = cudaGetDeviceProperties(&prop, p->device)) != cudaSuccess) { delete p; return cuda_fail(e, "plan: properties"); }
   p->sms = prop.multiProcessorCount;
   p->smem_optin = prop.sharedMemPerBlockOptin;
-  const long vec = 16 / (long)p->elem;
   size_t ws_bytes = 0;
   long max_partials = 0;
   for (int i = 0; i < count; ++i) {
-    GridDesc g;
-    g.nx = nx[i];
-    g.ny = ny[i];
-    g.off = vec - 1;
-    g.pitch = ((g.off + g.nx + 2) + vec - 1) / vec * vec;
+    GridDesc g = plan_layout(dt, nx[i], ny[i]);
     for (int d = 0; d < 5; ++d) g.w[d] = dt == J2D_F64 ? w[5 * i + d] : (double)(float)w[5 * i + d];
     p->grids.push_back(g);
     p->ws_off.push_back(ws_bytes);
@@ -561,6 +556,9 @@ static std::string tune_key(j2d5pt_plan_t p, long steps) {
   long b = 1;
   while (b < steps) b <<= 1;
   k += "|" + std::to_string(b);
+  // the cache file separates fields by whitespace: the key holds none
+  for (char &ch : k)
+    if (ch == ' ' || ch == '\t') ch = '_';
   return k;
 }
 

@@ -21,6 +21,19 @@ struct GridDesc {
   size_t bytes(size_t elem) const { return (size_t)(ny + 2) * (size_t)pitch * elem; }
 };
 
+// The plan layout of an nx*ny grid (include/j2d5pt.h): logical column 0 at
+// element offset 16/sizeof-1, so interior column 1 starts a 16-byte vector;
+// rows padded to whole 16-byte vectors.  Weights left zero.
+inline GridDesc plan_layout(j2d_dtype dt, int nx, int ny) {
+  GridDesc g;
+  const long vec = dt == J2D_F64 ? 2 : 4;
+  g.nx = nx;
+  g.ny = ny;
+  g.off = vec - 1;
+  g.pitch = ((g.off + nx + 2) + vec - 1) / vec * vec;
+  return g;
+}
+
 // Geometry of the temporally blocked kernels (chosen by the planner / tuner).
 struct DtbConfig {
   int algo = J2D_ALGO_ONESTEP;  // resolved algorithm

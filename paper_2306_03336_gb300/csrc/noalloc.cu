@@ -10,6 +10,9 @@
 // latency-bound loops that cannot absorb cudaFree's implicit device-wide
 // synchronisation.  This file gives them the same reduction with its scratch
 // in a fixed device array compiled into the library.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -23,10 +26,29 @@ namespace j2d {
 constexpr long kNoAllocMaxBlocks = 65536;
 static __device__ __align__(256) double g_wgrad_scratch[5 * kNoAllocMaxBlocks];
 
-// Device address of the array, looked up once per device.
+// Device address of the array, looked up once per device and context: a
+// context that was torn down and created again (cudaDeviceReset) loads the
+// module afresh, possibly at another address, so the address is looked up
+// again whenever the current context differs from the one it was taken in.
 constexpr int kMaxDevices = 128;
 static double *g_scratch_addr[kMaxDevices];
+static CUcontext g_scratch_ctx[kMaxDevices];
 static std::mutex g_scratch_mu;
+
+// cuCtxGetCurrent through the runtime's driver entry point (no -lcuda).
+static CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuCtxGetCurrent_v4000)f;
+  }
+  CUcontext c = nullptr;
+  if (fn) fn(&c);
+  return c;
+}
 
 }  // namespace j2d
 
@@ -39,13 +61,7 @@ extern "C" j2d_status j2d5pt_weight_grad_noalloc(int nx, int ny, j2d_dtype dtype
   if (!u_t || !lam_t1 || !dw) return record_error(J2D_ERR_ARG, "weight_grad_noalloc: null pointer");
   if (((uintptr_t)u_t & 15u) || ((uintptr_t)lam_t1 & 15u) || ((uintptr_t)dw & 7u))
     return record_error(J2D_ERR_ALIGN, "weight_grad_noalloc: u_t/lam_t1 must be 16-byte and dw 8-byte aligned");
-  // the plan layout for this grid (same rule as j2d5pt_plan)
-  GridDesc g;
-  g.nx = nx;
-  g.ny = ny;
-  const long vec = dtype == J2D_F64 ? 2 : 4;
-  g.off = vec - 1;
-  g.pitch = (g.off + nx + 2 + vec - 1) / vec * vec;
+  const GridDesc g = plan_layout(dtype, nx, ny);  // the layout j2d5pt_plan gives this grid
   const long nblocks = wgrad_partial_count(dtype, g);
   if (nblocks > kNoAllocMaxBlocks)
     return record_error(J2D_ERR_ARG,
@@ -59,14 +75,17 @@ extern "C" j2d_status j2d5pt_weight_grad_noalloc(int nx, int ny, j2d_dtype dtype
   double *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-      // set-up, once per device, with that device current: the host-side name
-      // of the array is not a device address
+    const CUcontext ctx = current_context();
+    if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
+      // set-up, once per device (and again after its context was replaced),
+      // with that device current: the host-side name of the array is not a
+      // device address
       double *p = nullptr;
       e = cudaGetSymbolAddress((void **)&p, g_wgrad_scratch);
       if (e != cudaSuccess)
         return record_error(J2D_ERR_DEVICE, "weight_grad_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
       g_scratch_addr[dev] = p;
+      g_scratch_ctx[dev] = current_context();
     }
     scratch = g_scratch_addr[dev];
   }

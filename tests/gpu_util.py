@@ -36,3 +36,37 @@ def f32_bound(steps):
     weight rounding (sum off by up to 5 * 2^-24 per step) and per-step
     rounding (up to 6 * 2^-24), accumulated linearly."""
     return (1 + 12 * max(steps, 1)) * 2.0 ** -24
+
+
+def window_block(oracle, u0, w, steps, y0, y1, x0, x1, threads=None):
+    """Oracle values of the cells [y0, y1) x [x0, x1) of u0 (array coordinates,
+    ring included) after `steps` steps.  A cell's value after T steps depends
+    only on the initial cells within distance T, so the oracle runs on the
+    block plus a margin of T+1 cells (clipped at the array; the margin's edge is
+    held constant, and its changes cannot reach the block within T steps)."""
+    H, W = u0.shape
+    r = steps + 1
+    a0, a1 = max(0, y0 - r), min(H, y1 + r)
+    b0, b1 = max(0, x0 - r), min(W, x1 + r)
+    win = np.ascontiguousarray(u0[a0:a1, b0:b1])
+    if threads is None:
+        threads = oracle.max_threads()
+    out = oracle.run(win, w, steps, threads=threads)
+    return out[y0 - a0:y1 - a0, x0 - b0:x1 - b0]
+
+
+def blocks_for(ny, nx, size=300):
+    """Blocks (y0, y1, x0, x1) that cover the grid's corners (ring-adjacent
+    cells, the first and last tiles), its middle and the middle of its left
+    and bottom edges; each is `size` cells square (clipped), large enough to
+    contain tile seams and CTA-group edges of every tile shape in both axes."""
+    H, W = ny + 2, nx + 2
+    s = min(size, H, W)
+    cy, cx = (H - s) // 2, (W - s) // 2
+    out = [(0, s, 0, s), (H - s, H, W - s, W), (cy, cy + s, cx, cx + s), (cy, cy + s, 0, s), (H - s, H, cx, cx + s)]
+    seen, res = set(), []
+    for b in out:
+        if b not in seen:
+            seen.add(b)
+            res.append(b)
+    return res

@@ -22,7 +22,7 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["value"] > 0 and d["unit"] == "GCells/s" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
-    assert d["config"]["workload"] == "j2d5pt_f64_2048x1536_1000"
+    assert d["config"]["workload"] == "j2d5pt_f64_16384x16384_1000"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]

@@ -72,7 +72,7 @@ def test_argument_errors_before_device(lib):
 
 def test_arith_info_without_gpu(lib):
     """The FP64 cell-evaluation contract is a property of the library: half of
-    the cells (rows with y mod 4 in {0, 1}) on the integer path, 18 guard bits."""
+    the cells (rows with y mod 4 in {0, 1}) on the integer path, 11 guard bits."""
     m, g = ctypes.c_uint(), ctypes.c_int()
     assert lib.j2d5pt_arith_info(ctypes.byref(m), ctypes.byref(g)) == j2d5pt.J2D_OK
     assert m.value == 0x0F and g.value == 11

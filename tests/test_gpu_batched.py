@@ -67,19 +67,33 @@ def test_batched_cuda_graph_replay():
         assert np.array_equal(a, b)
 
 
-def test_batched_workload_256_grids_sampled():
-    # the benchmark batch: 256 grids, sides uniform in [64, 1024], 200 steps;
-    # checked against the oracle on a sample of grids
+def test_batched_workload_256_grids_all():
+    """The benchmark batch (256 grids, sides uniform in [64, 1024], 200 steps)
+    in the benchmark's launch configuration (autotuned, CUDA graph): every
+    grid bit for bit against its own single-grid one-step run on the device,
+    and a sample of grids against the oracle."""
+    import torch
     cfg = synth.WORKLOADS["j2d5pt_f64_batch256_200"]
     sizes = synth.batch_sizes(cfg["count"], synth.data_seed(cfg["index"]), cfg["lo"], cfg["hi"])
-    import torch
     w = np.stack([synth.weights(synth.weight_seed(cfg["index"]) + i) for i in range(len(sizes))])
-    p = j2d5pt.Plan.batch(sizes, "f64", w).set("algo", "tiles").set("depth", 8)
+    p = j2d5pt.Plan.batch(sizes, "f64", w)
     us = [synth.field(nx, ny, synth.data_seed(cfg["index"]) + 10 + i) for i, (nx, ny) in enumerate(sizes)]
     srcs = [p.to_device(u, i) for i, u in enumerate(us)]
     dsts = [p.empty(i) for i in range(len(sizes))]
-    p.run_batched(srcs, dsts, cfg["steps"])
-    p.sync()
+    p.autotune_batched(srcs, dsts, cfg["steps"])
+    p.set("graph", 1)
+    for _ in range(2):  # capture, then replay
+        for d in dsts:
+            d.zero_()
+        p.run_batched(srcs, dsts, cfg["steps"])
+        p.sync()
+    for i, (nx, ny) in enumerate(sizes):
+        q = j2d5pt.Plan(nx, ny, "f64", w[i]).set("algo", "onestep")
+        out = q.empty()
+        q.run(srcs[i], out, cfg["steps"])
+        q.sync()
+        assert torch.equal(q.view(out), p.view(dsts[i], i)), (i, nx, ny, p.describe())
+        q.close()
     for i in (0, 17, 100, 255):
         ref = oracle.run(us[i], w[i], cfg["steps"], threads=oracle.max_threads())
         assert rel_err(p.to_host(dsts[i], i), ref) <= TOL_F64
