@@ -55,6 +55,12 @@ def _load():
         lib.oracle_j2d5pt_grad.restype = I
         lib.oracle_dot.argtypes = [I, I, P, P]
         lib.oracle_dot.restype = ctypes.c_double
+        lib.oracle_j2d9pt_step.argtypes = [I, I, P, P, P]
+        lib.oracle_j2d9pt_step.restype = None
+        lib.oracle_j2d9pt_run.argtypes = [I, I, P, P, P, L, I]
+        lib.oracle_j2d9pt_run.restype = I
+        lib.oracle_j2d9pt_run_f32.argtypes = [I, I, P, P, P, L, I]
+        lib.oracle_j2d9pt_run_f32.restype = I
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = I
         _lib = lib
@@ -167,3 +173,42 @@ def dot(a, b):
 def loss(u, g):
     """L = <g, u>."""
     return dot(g, u)
+
+
+# ---- j2d9pt: the nine-point box stencil --------------------------------------
+
+def _w9(w, dtype=np.float64):
+    w = np.ascontiguousarray(w, dtype=dtype).reshape(-1)
+    if w.size != 9:
+        raise ValueError("box weights must be nine values, rows y-1, y, y+1 and columns x-1, x, x+1")
+    return w
+
+
+def box_step(u, w):
+    """One step of the 3x3 box stencil (weights row by row from the y-1 row,
+    x-1 first), ring held constant."""
+    u, nx, ny = _grid(u)
+    w = _w9(w)
+    out = np.empty_like(u)
+    _load().oracle_j2d9pt_step(nx, ny, _p(w), _p(u), _p(out))
+    return out
+
+
+def box_run(u0, w, steps, threads=1):
+    """``steps`` steps of the 3x3 box stencil."""
+    u0, nx, ny = _grid(u0)
+    w = _w9(w)
+    out = np.empty_like(u0)
+    if _load().oracle_j2d9pt_run(nx, ny, _p(w), _p(u0), _p(out), int(steps), int(threads)):
+        raise MemoryError("oracle box_run: allocation failed")
+    return out
+
+
+def box_run_f32(u0, w, steps, threads=1):
+    """The box iteration in binary32 storage and arithmetic (weights rounded to float)."""
+    u0, nx, ny = _grid(u0, np.float32)
+    w = _w9(w, np.float32)
+    out = np.empty_like(u0)
+    if _load().oracle_j2d9pt_run_f32(nx, ny, _p(w), _p(u0), _p(out), int(steps), int(threads)):
+        raise MemoryError("oracle box_run_f32: allocation failed")
+    return out

@@ -245,6 +245,111 @@ int oracle_j2d5pt_grad(int nx, int ny, const double *w, const double *u0, const 
   return 0;
 }
 
+/* ---- j2d9pt: the nine-point box stencil -------------------------------------
+ *
+ * The paper presents j2d5pt as a case study of deep temporal blocking (title,
+ * Section 1); its step function (Section 3.1) does not depend on the shape of
+ * the stencil.  The second shape built here is the 3x3 box:
+ *   out[y][x] = sum over dy = -1, 0, 1 and dx = -1, 0, 1 of
+ *               w[3*(dy+1) + (dx+1)] * in[y+dy][x+dx]
+ * i.e. weights in the order (y-1: x-1, x, x+1), (y: x-1, x, x+1),
+ * (y+1: x-1, x, x+1), the y-1 row first as the paper's S link reads the row
+ * below.  Summed left to right in that order, binary64, no fused
+ * multiply-add, out of place; the one-cell ring is held constant. */
+static void box_rows(int nx, int ny, const double *w, const double *in, double *out, int nthreads) {
+  int y;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (y = 1; y <= ny; ++y) {
+    for (int x = 1; x <= nx; ++x) {
+      double acc = w[0] * in[IDX(y - 1, x - 1)];
+      acc = acc + w[1] * in[IDX(y - 1, x)];
+      acc = acc + w[2] * in[IDX(y - 1, x + 1)];
+      acc = acc + w[3] * in[IDX(y, x - 1)];
+      acc = acc + w[4] * in[IDX(y, x)];
+      acc = acc + w[5] * in[IDX(y, x + 1)];
+      acc = acc + w[6] * in[IDX(y + 1, x - 1)];
+      acc = acc + w[7] * in[IDX(y + 1, x)];
+      acc = acc + w[8] * in[IDX(y + 1, x + 1)];
+      out[IDX(y, x)] = acc;
+    }
+  }
+  (void)nthreads;
+  for (int x = 0; x < nx + 2; ++x) {
+    out[IDX(0, x)] = in[IDX(0, x)];
+    out[IDX(ny + 1, x)] = in[IDX(ny + 1, x)];
+  }
+  for (int yy = 1; yy <= ny; ++yy) {
+    out[IDX(yy, 0)] = in[IDX(yy, 0)];
+    out[IDX(yy, nx + 1)] = in[IDX(yy, nx + 1)];
+  }
+}
+
+void oracle_j2d9pt_step(int nx, int ny, const double *w, const double *in, double *out) {
+  box_rows(nx, ny, w, in, out, 1);
+}
+
+int oracle_j2d9pt_run(int nx, int ny, const double *w, const double *u0, double *uT, long steps, int nthreads) {
+  size_t n = (size_t)(nx + 2) * (size_t)(ny + 2);
+  double *a = (double *)malloc(n * sizeof(double));
+  double *b = (double *)malloc(n * sizeof(double));
+  if (!a || !b) { free(a); free(b); return 1; }
+  memcpy(a, u0, n * sizeof(double));
+  for (long t = 0; t < steps; ++t) {
+    box_rows(nx, ny, w, a, b, nthreads);
+    double *tmp = a; a = b; b = tmp;
+  }
+  memcpy(uT, a, n * sizeof(double));
+  free(a);
+  free(b);
+  return 0;
+}
+
+/* The same iteration in binary32 storage and arithmetic (weights rounded to
+ * float), no FMA. */
+int oracle_j2d9pt_run_f32(int nx, int ny, const float *w, const float *u0, float *uT, long steps, int nthreads) {
+  size_t n = (size_t)(nx + 2) * (size_t)(ny + 2);
+  float *a = (float *)malloc(n * sizeof(float));
+  float *b = (float *)malloc(n * sizeof(float));
+  if (!a || !b) { free(a); free(b); return 1; }
+  memcpy(a, u0, n * sizeof(float));
+  for (long t = 0; t < steps; ++t) {
+    int y;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (y = 1; y <= ny; ++y) {
+      for (int x = 1; x <= nx; ++x) {
+        float acc = w[0] * a[IDX(y - 1, x - 1)];
+        acc = acc + w[1] * a[IDX(y - 1, x)];
+        acc = acc + w[2] * a[IDX(y - 1, x + 1)];
+        acc = acc + w[3] * a[IDX(y, x - 1)];
+        acc = acc + w[4] * a[IDX(y, x)];
+        acc = acc + w[5] * a[IDX(y, x + 1)];
+        acc = acc + w[6] * a[IDX(y + 1, x - 1)];
+        acc = acc + w[7] * a[IDX(y + 1, x)];
+        acc = acc + w[8] * a[IDX(y + 1, x + 1)];
+        b[IDX(y, x)] = acc;
+      }
+    }
+    for (int x = 0; x < nx + 2; ++x) {
+      b[IDX(0, x)] = a[IDX(0, x)];
+      b[IDX(ny + 1, x)] = a[IDX(ny + 1, x)];
+    }
+    for (int yy = 1; yy <= ny; ++yy) {
+      b[IDX(yy, 0)] = a[IDX(yy, 0)];
+      b[IDX(yy, nx + 1)] = a[IDX(yy, nx + 1)];
+    }
+    float *tmp = a; a = b; b = tmp;
+  }
+  memcpy(uT, a, n * sizeof(float));
+  free(a);
+  free(b);
+  (void)nthreads;
+  return 0;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

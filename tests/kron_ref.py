@@ -57,3 +57,24 @@ def to_fraction(a):
     for i, v in enumerate(flat):
         of[i] = Fraction(float(v))
     return out
+
+
+def full_matrix_box(nx, ny, w, exact=False):
+    """One step of the 3x3 box stencil (j2d9pt) as a matrix: the interior
+    block is sum over dy, dx in {-1, 0, 1} of w[3*(dy+1) + (dx+1)] times
+    (Dy^dy kron Dx^dx), where D^d reads the neighbour at offset d; ring rows
+    are the identity."""
+    ws = [Fraction(v) for v in w] if exact else [float(v) for v in w]
+    one = Fraction(1) if exact else 1.0
+    X, Y = nx + 2, ny + 2
+    A = None
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            term = ws[3 * (dy + 1) + (dx + 1)] * np.kron(shift(Y, dy, one), shift(X, dx, one))
+            A = term if A is None else A + term
+    ring = np.ones((Y, X), dtype=bool)
+    ring[1:-1, 1:-1] = False
+    ring = ring.reshape(-1)
+    Id = np.kron(shift(Y, 0, one), shift(X, 0, one))
+    A[ring, :] = Id[ring, :]
+    return A
