@@ -585,7 +585,9 @@ WORKLOADS = {
     "f64tiles": (8192, 8192, "f64", "tiles", 4, 4, 8, 1),
     "f64resident": (2048, 1536, "f64", "resident", 0, 0, 1000, 1),
     "f64onestep": (2048, 1536, "f64", "onestep", 0, 0, 8, 1),
+    "f64skewed": (8192, 8192, "f64", "skewed", 4, 4, 8, 1),
     "f32tiles": (8192, 8192, "f32", "tiles", 16, 2, 16, 1),
+    "f32skewed": (8192, 8192, "f32", "skewed", 16, 8, 32, 1),
     "f32onestep": (8192, 8192, "f32", "onestep", 0, 0, 4, 1),
 }
 

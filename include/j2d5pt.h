@@ -65,14 +65,19 @@ typedef enum {
   J2D_ALGO_ONESTEP = 1,  /* one launch per time step, streaming through HBM */
   J2D_ALGO_RESIDENT = 2, /* whole grid held on chip for all steps; one persistent launch */
   J2D_ALGO_BANDS = 3,    /* GPU-wide bands of the grid, processed serially, k steps per visit */
-  J2D_ALGO_TILES = 4     /* independent per-CTA tiles with a k-deep overlapped halo */
+  J2D_ALGO_TILES = 4,    /* independent per-CTA tiles with a k-deep overlapped halo */
+  J2D_ALGO_SKEWED = 5    /* serial tiles in skewed order: each CTA advances a run of rows of a
+                            column band tile after tile, k steps per visit, each tile taking its
+                            top halo at every step from the tile before it (no overlapped halo
+                            in y; the k-deep overlap stays in x).  Forward runs only (adjoint
+                            runs of a plan set to it take TILES). */
 } j2d_algo;
 
 /* Plan options (j2d5pt_set_option / j2d5pt_get_option). */
 typedef enum {
   J2D_OPT_ALGO = 0,       /* j2d_algo */
-  J2D_OPT_DEPTH = 1,      /* temporal depth k (steps per on-chip visit) for BANDS / TILES */
-  J2D_OPT_TILE_WX = 2,    /* TILES: warp strips across a CTA tile (16 / WX down) */
+  J2D_OPT_DEPTH = 1,      /* temporal depth k (steps per on-chip visit) for BANDS / TILES / SKEWED */
+  J2D_OPT_TILE_WX = 2,    /* TILES / SKEWED: warp strips across a CTA tile (16 / WX down) */
   J2D_OPT_CTAS = 3,       /* persistent grid size (0 = one CTA per SM) */
   J2D_OPT_TIMEOUT_MS = 4, /* device-side wait limit in milliseconds (default 2000) */
   J2D_OPT_VERBOSE = 5,    /* 1 = print the chosen configuration to stderr at run time */

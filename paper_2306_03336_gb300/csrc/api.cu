@@ -194,7 +194,7 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
   if (!p) return fail(J2D_ERR_ARG, "set_option: null plan");
   switch (opt) {
     case J2D_OPT_ALGO:
-      if (v < J2D_ALGO_AUTO || v > J2D_ALGO_TILES) return fail(J2D_ERR_ARG, "set_option: bad algo %ld", v);
+      if (v < J2D_ALGO_AUTO || v > J2D_ALGO_SKEWED) return fail(J2D_ERR_ARG, "set_option: bad algo %ld", v);
       p->opt_algo = (int)v;
       drop_graph(p);
       break;
@@ -290,6 +290,7 @@ static const char *algo_name(int a) {
     case J2D_ALGO_RESIDENT: return "resident";
     case J2D_ALGO_BANDS: return "bands";
     case J2D_ALGO_TILES: return "tiles";
+    case J2D_ALGO_SKEWED: return "skewed";
     default: return "auto";
   }
 }
@@ -536,7 +537,8 @@ extern "C" j2d_status j2d5pt_sync_status(j2d5pt_plan_t p) {
 }
 
 // Autotuner.  Candidates: the one-step kernel; the resident kernel when the
-// grid fits on chip; bands and tiles over temporal depths k (and tile shapes).
+// grid fits on chip; bands, tiles and skewed tiles over temporal depths k
+// (and tile shapes).
 // Each is timed with CUDA events for min(steps, 64) steps (best of two runs
 // after a warm-up run); the fastest is kept in the plan.  With J2D_TUNE_CACHE set, results are
 // read from / appended to that file, keyed by device, SM count, dtype, grid
@@ -617,6 +619,7 @@ static j2d_status autotune_common(j2d5pt_plan_t p, const void *const *in, void *
     if (d > steps) break;
     if (single) cands.push_back({J2D_ALGO_BANDS, d, 0});
     for (int wx : {1, 2, 4}) cands.push_back({J2D_ALGO_TILES, d, wx});
+    for (int wx : {2, 4, 8}) cands.push_back({J2D_ALGO_SKEWED, d, wx});
   }
   float best_ms = 1e30f;
   Cand best = {J2D_ALGO_AUTO, 0, 0};

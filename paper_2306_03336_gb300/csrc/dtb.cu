@@ -23,14 +23,18 @@
 // back with per-row TMA tensor stores (the store tensor map ends at the last
 // interior row/column, so the ring and padding are never written).
 //
-// Three schedules drive the same strip code:
+// Four schedules drive the same strip code:
 //   RESIDENT  all strips of the grid on chip at once, every step exchanged
 //             (the grid must fit in the GPU's shared memory);
 //   BANDS     the paper's serial GPU-wide tiles: full-width bands of rows
 //             with a k-row overlapped halo above and below, k steps per visit;
 //   TILES     independent CTA tiles with a k-deep overlapped halo on all sides
 //             (no cross-CTA exchange at all), k steps per visit; also carries
-//             batches of grids, partial tiles packed side by side in a CTA.
+//             batches of grids, partial tiles packed side by side in a CTA;
+//   SKEWED    serial tiles in skewed coordinates: each CTA advances a run of
+//             rows of a column band tile after tile, each tile taking its top
+//             halo at every step from the tile before it, so no halo is
+//             recomputed in y (run_strip_skew).
 // In RESIDENT and BANDS a CTA holds a block of strips (4 x 4 where the grid
 // allows; see choose_bx), so that most neighbours share its shared memory.
 // FP32 TILES strips take two steps per exchange (run_strip_pair), reading
@@ -56,13 +60,20 @@ constexpr int kWarps = 16;            // warps (strips) per CTA
 constexpr int kThreads = kWarps * 32;
 enum { SIDE_YM = 0, SIDE_YP = 1, SIDE_XM = 2, SIDE_XP = 3 };
 enum { LINK_CONST = -1, LINK_ZERO = -2 };
-enum { MODE_BANDS = 0, MODE_TILES = 1, MODE_TILES_PAIR = 2 };
+enum { MODE_BANDS = 0, MODE_TILES = 1, MODE_TILES_PAIR = 2, MODE_SKEW = 3 };
 // A tile job: grid, tile origin (x, y), valid core [vx0, vx1) x [vy0, vy1),
 // first warp, strips across and down (only the strips inside the grid: a
 // CTA runs a group of partial tiles side by side), and in the first tile of
 // a group the number of tiles in the group (so that a group is read with its
 // first record, no extra indirection).
 constexpr int kTileInts = 11;
+// A skewed tile job (SKEWED schedule): grid, band origin tx0 and valid
+// columns [vx0, vx1), first skewed row q0 and row count nq of the tile, the
+// physical rows [v0, v1) of the tile's piece whose values the tile stores
+// (skewed rows [v0+k, v1+k) at level k), first = 1 when the tile opens a
+// piece (no predecessor in the CTA's list), and wxa, the strips across
+// inside the grid.
+constexpr int kSkewInts = 10;
 
 // Per-grid data the kernel reads from global memory.
 struct GridDev {
@@ -90,6 +101,8 @@ struct KParams {
   unsigned long long timeout_ns;
   int mute_slot;            // fault injection: this slot never publishes its step counter (-1: none)
   int int_path;             // FP64: the kExactMask cells on the integer path
+  void *skewbuf;            // SKEWED: per CTA [2 parities][levels][2 rows][skew_tw] elements
+  int skew_tw, skew_levels, skew_wx;  // SKEWED: band width (elements), levels per parity, strips across
 };
 
 // Layout of one warp's shared-memory region (elements of T).
@@ -934,6 +947,268 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
   strip_store<T, false>(st, gd, data, map_store, dstbuf, lane, rg);
 }
 
+// ---- skewed serial tiles (SKEWED) -------------------------------------------
+//
+// Sections 3.1-3.3 and Figure 1 advance tiles one after another.  With a
+// k-deep overlapped halo each tile recomputes its neighbours' edge cells; in
+// skewed coordinates a tile takes them from its predecessor instead.  Skewed
+// row q at time level t holds physical row y = q - t.  An update to level
+// t+1 then reads, at level t, the skewed rows q-2 (the y-1 link), q-1 (the
+// centre and its x-1 and x+1 links) and q (the y+1 link): the row itself and
+// rows above it, never rows below.  So a column band is advanced k levels
+// tile after tile from the top: a tile needs, at every level, the last two
+// rows of the tile above it, and no halo below.  A CTA owns a contiguous run
+// of the skewed rows of one or more column bands (a "piece" per band) and
+// processes its tiles in order, handing the last two rows of each level to
+// the next tile through a per-CTA buffer in global memory (double-buffered by
+// tile parity).  A piece that starts inside a band starts 2(k-1) rows early:
+// its top halo holds the level-0 rows at every level, which spoils 2(j-1)
+// rows by level j.  Columns keep the overlapped halo of the TILES schedule.
+// Cells whose physical row lies outside the interior (the ring rows, rows
+// beyond the array) take the identity update, i.e. the value of their centre
+// operand; the ring columns are read at the shifted row.  Every cell is
+// evaluated with the same operands in the same order as in the one-step
+// kernel, so results are bit-identical.  Inside a tile the neighbours' cells
+// are read in place between two CTA barriers per step.
+
+// A warp's region: its strip (R rows) and two 32-entry halo columns.
+__host__ __device__ inline int skew_region_elems(int elem, int rmax) {
+  const int SW = 32 * (16 / elem);
+  const int per128 = 128 / elem;
+  return (rmax * SW + 64 + per128 - 1) / per128 * per128;
+}
+__host__ __device__ inline size_t skew_smem_bytes(int elem, int rmax) {
+  return (size_t)kHeaderBytes + (size_t)kWarps * skew_region_elems(elem, rmax) * elem;
+}
+
+// One step over a strip in skewed coordinates, swept top-down and updated in
+// place: new row r from the old rows r-2 (the y-1 link), r-1 (the centre with
+// its x-1 and x+1 links) and r (the y+1 link); ta, tb are rows -2 and -1.
+// Rows [r_lo, r_hi) take the stencil, the others (physical row outside the
+// interior) the identity.  yb: physical row of new row 0.
+template <typename T, bool DEAD>
+__device__ __forceinline__ void sweep_skew(T *drow, const T *hct, int rows, int r_lo, int r_hi, int lane,
+                                           const Links<T> &a, const ExactW &u, bool ip, int xl, int yb,
+                                           const T (&ta)[VecOf<T>::V], const T (&tb)[VecOf<T>::V],
+                                           uint32_t dead) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  T ra[V], rb[V], rc[V], o[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    ra[e] = ta[e];
+    rb[e] = tb[e];
+  }
+  int r = 0;
+  for (; r < r_lo; ++r) {
+    vload(drow + r * SW, false, rc);
+    vstore(drow + r * SW, rb);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      ra[e] = rb[e];
+      rb[e] = rc[e];
+    }
+  }
+  // every row loads itself (no halo below): the body is the same for all
+  // rows, unrolled by the window's period for FP32 as in sweep_rows
+  constexpr int kUnroll = sizeof(T) == 4 ? 3 : 2;
+#pragma unroll kUnroll
+  for (; r < r_hi; ++r) {
+    vload(drow + r * SW, false, rc);
+    row_update<T, DEAD>(ra, rb, rc, hct[r], hct[r], lane, a, u, ip, xl, yb + r, dead, o);
+    vstore(drow + r * SW, o);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      ra[e] = rb[e];
+      rb[e] = rc[e];
+    }
+  }
+  for (; r < rows; ++r) {
+    vload(drow + r * SW, false, rc);
+    vstore(drow + r * SW, rb);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      ra[e] = rb[e];
+      rb[e] = rc[e];
+    }
+  }
+}
+
+// Advance this warp's strip of one skewed tile (job) by k levels: load level
+// 0, k steps, store level k.  Called by every warp of the CTA with the same k.
+template <typename T>
+__device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, int warp, int src, int dst, int k,
+                               int par, uint32_t &mbar_phase, const Prefetch &pf) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  const int lane = threadIdx.x & 31;
+  const int R = kp.rmax;
+  const int region = skew_region_elems((int)sizeof(T), R);
+  T *wbase = reinterpret_cast<T *>(smem + kHeaderBytes);
+  T *data = wbase + (size_t)warp * region;
+  T *hc = data + (size_t)R * SW;  // [2][32]: entry r = halo column x-1 (then x+SW) at strip row r-1
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  const int g = job[0], tx0 = job[1], vx0 = job[2], vx1 = job[3], q0 = job[4], nq = job[5], v0 = job[6],
+            v1 = job[7];
+  const bool first = job[8] != 0;
+  const int wxa = job[9];
+  const int WX = kp.skew_wx;
+  const int wx = warp % WX, wy = warp / WX;
+  const GridDev &gd = kp.grids[g];
+  const int nx = gd.nx, ny = gd.ny;
+  const long pitch = gd.pitch;
+  const int off = gd.off;
+  const int x0 = tx0 + wx * SW, y0 = q0 + wy * R;
+  const int rows = min(R, q0 + nq - y0);
+  const bool act = wx < wxa && rows > 0;
+  const T *srcbuf = reinterpret_cast<const T *>(gd.buf[src]);
+  T *dstbuf = reinterpret_cast<T *>(gd.buf[dst]);
+  const CUtensorMap *map_load = kp.maps + (size_t)g * 6 + src;
+  const CUtensorMap *map_store = kp.maps + (size_t)g * 6 + 3 + dst;
+  const Links<T> a{(T)gd.w[0], (T)gd.w[1], (T)gd.w[2], (T)gd.w[3], (T)gd.w[4]};
+  ExactW u{};
+  if constexpr (std::is_same<T, double>::value) u = exact_weights(a);
+  const bool ip = kp.int_path != 0;
+  // neighbours in the tile (the strip above is full whenever this one has rows)
+  const int wT = wy > 0 ? warp - WX : -1;
+  const int wL = wx > 0 ? warp - 1 : -1;
+  const int wR = wx + 1 < wxa ? warp + 1 : -1;
+  const int wTL = wT >= 0 && wL >= 0 ? warp - WX - 1 : -1;
+  const int wTR = wT >= 0 && wR >= 0 ? warp - WX + 1 : -1;
+  auto nbdata = [&](int w) { return wbase + (size_t)w * region; };
+  // the tile's last two rows at every level, for the next tile of the piece
+  T *sbuf = reinterpret_cast<T *>(kp.skewbuf) + (size_t)blockIdx.x * 2 * kp.skew_levels * 2 * kp.skew_tw;
+  auto sb = [&](int p, int lev, int row) { return sbuf + (((size_t)p * kp.skew_levels + lev) * 2 + row) * kp.skew_tw; };
+  const bool bottom = act && rows >= 2 && y0 + rows == q0 + nq;
+  auto gval = [&](int y, int x) -> T {
+    return (x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+  };
+
+  const int xl = x0 + lane * V;
+  T *drow = data + lane * V;
+  uint32_t dead = 0;
+#pragma unroll
+  for (int e = 0; e < V; ++e)
+    if (act && xl + e > nx) dead |= 1u << e;
+
+  // level-0 halo above a tile-top strip and the two level-0 corner cells
+  T t2c[V], t1c[V];
+  T cl0 = T(0), cr0 = T(0);
+  if (act) {
+    fence_proxy_async_all();  // earlier generic writes before the async-proxy load
+    __syncwarp();
+    if (lane == 0) {
+      bulk_wait_read_all();  // previous tile's stores have read shared memory
+      mbar_expect_tx(&bars[warp], (uint32_t)(SW * R * sizeof(T)));
+      tma_load_2d(data, map_load, off + x0, y0, &bars[warp]);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      t2c[e] = wT < 0 ? gval(y0 - 2, xl + e) : T(0);
+      t1c[e] = wT < 0 ? gval(y0 - 1, xl + e) : T(0);
+    }
+    if (lane == 0) {
+      cl0 = gval(y0 - 1, x0 - 1);
+      cr0 = gval(y0 - 1, x0 + SW);
+    }
+    wait_mbar(&bars[warp], mbar_phase, kp);
+    mbar_phase ^= 1u;
+    if (pf.map && lane == 0) tma_prefetch_2d(pf.map, pf.x, pf.y);
+  }
+  __syncthreads();  // every strip holds level 0
+
+  const T *hct = hc + (lane == 31 ? 32 : 0);
+  const bool any_dead = __any_sync(0xffffffffu, dead != 0);
+  // values a tile-top or tile-edge strip takes from global memory, loaded one
+  // level ahead (during the sweep before the step that reads them): the two
+  // halo rows above (the level-0 rows for the first tile of a piece, else the
+  // previous tile's rows), the two corner cells (lane 0) and the ring columns
+  T pa[V], pb[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    pa[e] = t2c[e];
+    pb[e] = t1c[e];
+  }
+  T pcl = cl0, pcr = cr0;
+  T phl = x0 == 1 ? gval(y0 + lane - 1, 0) : T(0);
+  T phr = x0 + SW == nx + 1 ? gval(y0 + lane - 1, nx + 1) : T(0);
+  for (int L = 1; L <= k; ++L) {
+    T ta[V], tb[V];  // rows -2 and -1 at level L-1
+    if (act) {
+      if (wT >= 0) {
+        const T *d = nbdata(wT) + lane * V;
+        vload(d + (R - 2) * SW, false, ta);
+        vload(d + (R - 1) * SW, false, tb);
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          ta[e] = pa[e];
+          tb[e] = pb[e];
+        }
+      }
+      if (lane < rows) {
+        // halo columns at strip row lane-1 (level L-1; the ring columns
+        // at the physical row y0 + lane - L, loaded ahead)
+        T hl, hr;
+        if (wL >= 0) hl = lane > 0 ? nbdata(wL)[(lane - 1) * SW + SW - 1] : wTL >= 0 ? nbdata(wTL)[(R - 1) * SW + SW - 1] : pcl;
+        else hl = phl;  // the ring column, or zero at a band edge (overlapped halo)
+        if (wR >= 0) hr = lane > 0 ? nbdata(wR)[(lane - 1) * SW] : wTR >= 0 ? nbdata(wTR)[(R - 1) * SW] : pcr;
+        else hr = phr;
+        hc[lane] = hl;
+        hc[32 + lane] = hr;
+      }
+    }
+    __syncthreads();  // every strip has read its neighbours' level-(L-1) cells
+    if (act) {
+      if (L < k) {
+        // the next level's values from global memory, in flight during the sweep
+        if (wT < 0 && !first) {
+          vload(sb(par ^ 1, L, 0) + (x0 - tx0) + lane * V, false, pa);
+          vload(sb(par ^ 1, L, 1) + (x0 - tx0) + lane * V, false, pb);
+          if (lane == 0) {
+            if (wL >= 0) pcl = sb(par ^ 1, L, 1)[x0 - 1 - tx0];
+            if (wR >= 0) pcr = sb(par ^ 1, L, 1)[x0 + SW - tx0];
+          }
+        }
+        if (x0 == 1) phl = gval(y0 + lane - L - 1, 0);
+        if (x0 + SW == nx + 1) phr = gval(y0 + lane - L - 1, nx + 1);
+      }
+      // rows whose physical row y0 + r - L is interior take the stencil, the rest the identity
+      const int r_lo = min(max(L + 1 - y0, 0), rows), r_hi = max(min(ny + L + 1 - y0, rows), r_lo);
+      if (any_dead)
+        sweep_skew<T, true>(drow, hct, rows, r_lo, r_hi, lane, a, u, ip, xl, y0 - L, ta, tb, dead);
+      else
+        sweep_skew<T, false>(drow, hct, rows, r_lo, r_hi, lane, a, u, ip, xl, y0 - L, ta, tb, dead);
+      if (bottom && L < k) {
+        __syncwarp();
+        T v[V];
+        vload(drow + (rows - 2) * SW, false, v);
+        vstore(sb(par, L, 0) + (x0 - tx0) + lane * V, v);
+        vload(drow + (rows - 1) * SW, false, v);
+        vstore(sb(par, L, 1) + (x0 - tx0) + lane * V, v);
+      }
+    }
+    if (L < k) __syncthreads();  // every strip holds level L
+  }
+  if (!act) return;
+  // store level k: physical rows [v0, v1) are the skewed rows [v0+k, v1+k)
+  Strip st{};
+  st.g = g;
+  st.x0 = x0;
+  st.y0 = y0 - k;
+  st.rows = rows;
+  st.ring = 0;
+  st.sy0 = max(v0 + k - y0, 0);
+  st.sy1 = min(v1 + k - y0, rows);
+  if (st.sy1 < st.sy0) st.sy1 = st.sy0;
+  st.sx0 = max(vx0 - x0, 0);
+  st.sx1 = min(min(vx1, nx + 1) - x0, SW);
+  if (st.sx1 < st.sx0) st.sx1 = st.sx0;
+  if (st.sx0 == 0 && x0 + st.sx1 >= min(vx1, nx + 1) && (vx1 > nx || st.sx1 == SW)) st.sx1 = SW;
+  const RingAcc<T> rg{};
+  strip_store<T, false>(st, gd, data, map_store, dstbuf, lane, rg);
+}
+
 // Strip of slot `slot` in a band wave: columns strip j, row strip i of m.
 __device__ Strip band_strip(const KParams &kp, const int *wave, int slot, int SWc) {
   Strip st{};
@@ -1092,7 +1367,31 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
     const int dst = ((kp.rounds - 1 - r) & 1) == 0 ? 2 : 1;
     const int src = r == 0 ? kp.src0 : (((kp.rounds - r) & 1) == 0 ? 2 : 1);
     const int k = r == kp.rounds - 1 ? kp.last_depth : kp.depth;
-    if (MODE == MODE_BANDS) {
+    if constexpr (MODE == MODE_SKEW) {
+      // this CTA's tiles in order; tile parity selects the halo-row buffer
+      const int jend = kp.job_off[blockIdx.x + 1];
+      int par = 0;
+      for (int j = kp.job_off[blockIdx.x]; j < jend; ++j, par ^= 1) {
+        const int *job = kp.jobs + (size_t)kSkewInts * j;
+        // this warp's strip of the next tile goes into L2 while this one runs
+        Prefetch pf;
+        if (j + 1 < jend) {
+          const int *nj = job + kSkewInts;
+          const int wx = warp % kp.skew_wx, wy = warp / kp.skew_wx;
+          if (wx < nj[9] && wy * kp.rmax < nj[5] && nj[4] + wy * kp.rmax <= kp.grids[nj[0]].ny + 1) {
+            pf.map = kp.maps + (size_t)nj[0] * 6 + src;
+            pf.x = kp.grids[nj[0]].off + nj[1] + wx * SWc;
+            pf.y = nj[4] + wy * kp.rmax;
+          }
+        }
+        run_strip_skew<T>(kp, job, smem, warp, src, dst, k, par, phase, pf);
+      }
+      if (lane == 0) {
+        bulk_wait_all();
+        fence_proxy_async_global();
+      }
+      grid_barrier(kp, epoch);
+    } else if (MODE == MODE_BANDS) {
       for (int wv = 0; wv < kp.njobs; ++wv, ++seq) {
         const Strip st = band_strip(kp, kp.jobs + 5 * wv, slot, SWc);
         run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
@@ -1155,6 +1454,13 @@ int dtb_rows_max_pair(j2d_dtype dt, size_t smem_optin) {
   return 0;
 }
 
+int dtb_rows_max_skew(j2d_dtype dt, size_t smem_optin) {
+  const int elem = dt == J2D_F64 ? 8 : 4;
+  for (int r = 32; r >= 2; --r)
+    if (skew_smem_bytes(elem, r) <= smem_optin) return r;
+  return 0;
+}
+
 static int vec_of(j2d_dtype dt) { return dt == J2D_F64 ? 2 : 4; }
 
 // Resident fit: strips per column m and rows per strip for one grid on `ctas` CTAs.
@@ -1213,6 +1519,7 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   }
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
   if (algo == J2D_ALGO_BANDS && !single) algo = J2D_ALGO_TILES;
+  if (algo == J2D_ALGO_SKEWED && rq.adjoint) algo = J2D_ALGO_TILES;  // the skewed order is forward only
   c.algo = algo;
   c.depth = rq.depth > 0 ? rq.depth : (dt == J2D_F64 ? 4 : 8);
   c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : (dt == J2D_F64 ? 4 : 2);
@@ -1222,6 +1529,11 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   if (algo == J2D_ALGO_TILES && dt == J2D_F32 && !rq.adjoint && rq.sweep_steps == 2) {
     c.sweep = 2;
     c.rows = dtb_rows_max_pair(dt, smem_optin);
+  }
+  if (algo == J2D_ALGO_SKEWED) {
+    c.rows = dtb_rows_max_skew(dt, smem_optin);
+    if (rq.depth <= 0) c.depth = dt == J2D_F64 ? 8 : 16;
+    if (rq.tile_wx <= 0) c.tile_wx = 4;
   }
   return c;
 }
@@ -1272,6 +1584,32 @@ static std::vector<int> cover(int n, int win, int g) {
   return out;
 }
 
+// Even covering of [1, n] for the skewed bands: the fewest windows of `win`
+// columns (with g-column halos inside) whose valid widths are equal multiples
+// of V, so that no band is much narrower than the others (the warps of a
+// tile move in lockstep: a narrow band would leave most of a CTA idle while
+// its rows still take a full tile's time).  Same triples as cover(); empty
+// when a window cannot hold its halos.
+static std::vector<int> cover_even(int n, int win, int g, int V) {
+  if (n <= win) return {1, 1, n + 1};
+  const int cap = win - 2 * g;  // valid width of an inner window
+  if (cap < V) return {};
+  int m = (n + cap - 1) / cap, wv = 0;
+  for (;; ++m) {
+    wv = ((n + m - 1) / m + V - 1) / V * V;
+    if (wv <= cap) break;
+  }
+  std::vector<int> out;
+  for (int i = 0; i < m; ++i) {
+    const int v = 1 + i * wv;
+    if (v > n) break;
+    out.push_back(i == 0 ? 1 : v - g);
+    out.push_back(v);
+    out.push_back(std::min(n + 1, v + wv));
+  }
+  return out;
+}
+
 static void ensure(void *&p, size_t &cap, size_t need, cudaError_t &err) {
   if (cap >= need) return;
   if (p) cudaFree(p);
@@ -1286,6 +1624,7 @@ static void *kernel_ptr(int mode, bool adj) {
   if constexpr (std::is_same<T, float>::value) {
     if (mode == MODE_TILES_PAIR) return (void *)dtb_kernel<float, false, MODE_TILES_PAIR>;
   }
+  if (mode == MODE_SKEW) return (void *)dtb_kernel<T, false, MODE_SKEW>;
   if (mode == MODE_BANDS) return adj ? (void *)dtb_kernel<T, true, MODE_BANDS> : (void *)dtb_kernel<T, false, MODE_BANDS>;
   return adj ? (void *)dtb_kernel<T, true, MODE_TILES> : (void *)dtb_kernel<T, false, MODE_TILES>;
 }
@@ -1298,10 +1637,13 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   const int ctas = r.cfg.ctas;
   // two steps per sweep: FP32 tiles of the forward map
   const bool pair = r.cfg.sweep == 2 && dt == J2D_F32 && r.cfg.algo == J2D_ALGO_TILES && !r.adjoint;
-  const int rmax = pair ? dtb_rows_max_pair(dt, r.smem_optin) : dtb_rows_max(dt, r.smem_optin, kWarps);
+  const bool skew = r.cfg.algo == J2D_ALGO_SKEWED;
+  if (skew && r.adjoint) { err = "the skewed schedule is forward only"; return cudaErrorNotSupported; }
+  const int rmax = skew ? dtb_rows_max_skew(dt, r.smem_optin)
+                        : pair ? dtb_rows_max_pair(dt, r.smem_optin) : dtb_rows_max(dt, r.smem_optin, kWarps);
   const int rp = (rmax + 3) / 4 * 4;
   if (rmax < 2) { err = "shared memory too small"; return cudaErrorNotSupported; }
-  const int mode = (r.cfg.algo == J2D_ALGO_TILES) ? MODE_TILES : MODE_BANDS;
+  const int mode = skew ? MODE_SKEW : (r.cfg.algo == J2D_ALGO_TILES) ? MODE_TILES : MODE_BANDS;
   const bool single = grids.size() == 1;
   if (mode == MODE_BANDS && !single) { err = "bands/resident need a single grid"; return cudaErrorNotSupported; }
 
@@ -1336,6 +1678,81 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
         const int be = std::min(g.ny + 1, bs + hb);
         const int mm = std::min(m, be - bs);
         jobs.insert(jobs.end(), {bs, be, cv[i + 1], ve, mm});
+      }
+    } else if (mode == MODE_SKEW) {
+      const int wx = r.cfg.tile_wx, wy = kWarps / wx;
+      const int tw = wx * SW, th = wy * rmax;
+      const int gx = (depth + V - 1) / V * V;
+      tkey = {ctas, wx, rmax, depth, (long)grids.size(), 1000};
+      for (const GridDesc &g : grids) {
+        tkey.push_back(g.nx);
+        tkey.push_back(g.ny);
+      }
+      tiles_cached = tkey == S.tiles_key;
+      if (tiles_cached) {
+        jobs = S.tiles_jobs;
+        job_off = S.tiles_off;
+      } else {
+        // column bands of every grid (k-deep overlapped halo in x), each
+        // carrying the physical rows [1, ny+1) stored at level k
+        struct Band { int g, tx0, vx0, vx1, wxa; };
+        std::vector<Band> bands;
+        long total = 0;
+        for (size_t gi = 0; gi < grids.size(); ++gi) {
+          const GridDesc &g = grids[gi];
+          auto cx = cover_even(g.nx, tw, gx, V);
+          if (cx.empty() || cx.back() != g.nx + 1) {
+            err = "tile too narrow for the temporal depth";
+            return cudaErrorNotSupported;
+          }
+          for (size_t b = 0; b + 2 < cx.size(); b += 3) {
+            int wxa = 0;
+            while (wxa < wx && cx[b] + wxa * SW <= g.nx) ++wxa;
+            bands.push_back({(int)gi, cx[b], cx[b + 1], cx[b + 2], wxa});
+            total += (long)g.ny;
+          }
+        }
+        // split the bands' rows (in band order) into `ctas` runs of equal
+        // length (a tile takes the same time whatever its width: its warps
+        // move in lockstep); a run is cut into pieces, one per band it touches
+        std::vector<std::vector<int>> lists(ctas);
+        long acc = 0;
+        int cta = 0;
+        // A piece of physical rows [v, ve) computes the skewed rows
+        // [q0, ve+k): its values at level k are rows v+k .. ve+k-1, and a
+        // piece starting inside the band starts 2(k-1) rows before v+k (its
+        // top halo is held at level 0).  A last round of fewer steps k' < k
+        // runs the same tiles: rows v+k' .. ve+k'-1 lie inside and are clean.
+        for (const Band &bd : bands) {
+          const GridDesc &g = grids[bd.g];
+          const int vend = g.ny + 1;
+          int v = 1;
+          while (v < vend) {
+            const long target = (long)((double)total * (cta + 1) / ctas);
+            const long room = target - acc;
+            int take = room > 0 ? (int)room : 1;
+            take = std::max(take, 4 * depth);  // no pieces much shorter than their overlap
+            if (cta == ctas - 1) take = vend - v;
+            const int ve = std::min(vend, v + take);
+            const int q0 = std::max(1, v + depth - 2 * (depth - 1));
+            const int qe = ve + depth;
+            for (int q = q0; q < qe; q += th) {
+              const int nq = std::min(th, qe - q);
+              lists[cta].insert(lists[cta].end(), {bd.g, bd.tx0, bd.vx0, bd.vx1, q, nq, v, ve, q == q0 ? 1 : 0, bd.wxa});
+            }
+            acc += (long)(ve - v);
+            v = ve;
+            if (acc >= target && cta < ctas - 1) ++cta;
+          }
+        }
+        job_off.push_back(0);
+        for (int b = 0; b < ctas; ++b) {
+          jobs.insert(jobs.end(), lists[b].begin(), lists[b].end());
+          job_off.push_back((int)(jobs.size() / kSkewInts));
+        }
+        S.tiles_key = tkey;
+        S.tiles_jobs = jobs;
+        S.tiles_off = job_off;
       }
     } else {
       const int wx = r.cfg.tile_wx, wy = kWarps / wx;
@@ -1373,7 +1790,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
       kp.tile_rows = trows;
     }
   }
-  const int njobs = (int)(jobs.size() / (mode == MODE_BANDS ? 5 : kTileInts));
+  const int njobs = (int)(jobs.size() / (mode == MODE_BANDS ? 5 : mode == MODE_SKEW ? kSkewInts : kTileInts));
   // TILES: tiles are packed into groups of at most 16 strips that one CTA runs
   // side by side (a tile keeps only its strips inside the grid, so the small
   // tiles of a batch share CTAs instead of leaving warps idle): largest tiles
@@ -1487,7 +1904,12 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   if (e != cudaSuccess) { err = "descriptor allocation"; return cudaErrorMemoryAllocation; }
   const size_t slot_bytes = (size_t)WarpLayout<double>::mailbox_elems(rp) * 8;  // sized for the larger type
   const size_t nslots = (size_t)ctas * kWarps;
-  const size_t scratch = 256 + nslots * sizeof(int) + (mode == MODE_BANDS ? nslots * slot_bytes : 0);
+  // SKEWED: per CTA, two parities x (k+1) levels x two rows x the band width
+  const size_t skew_tw = mode == MODE_SKEW ? (size_t)r.cfg.tile_wx * SW : 0;
+  const size_t skew_bytes = mode == MODE_SKEW ? (size_t)ctas * 2 * (depth + 1) * 2 * skew_tw * elem : 0;
+  const size_t skew_off = (256 + nslots * sizeof(int) + 255) / 256 * 256;
+  const size_t scratch = mode == MODE_SKEW ? skew_off + skew_bytes
+                                           : 256 + nslots * sizeof(int) + (mode == MODE_BANDS ? nslots * slot_bytes : 0);
   ensure(S.scratch, S.scratch_bytes, scratch, e);
   if (e != cudaSuccess) { err = "scratch allocation"; return cudaErrorMemoryAllocation; }
   // upload the descriptors unless the device copy already holds them (a run
@@ -1549,8 +1971,15 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   // CTA block
   kp.mute_slot = r.mute_slot < 0 ? -1 : (kp.bx > 0 ? kp.bx - 1 : 0);
   kp.int_path = r.int_path;
+  if (mode == MODE_SKEW) {
+    kp.skewbuf = sc + skew_off;
+    kp.skew_tw = (int)skew_tw;
+    kp.skew_levels = depth + 1;
+    kp.skew_wx = r.cfg.tile_wx;
+  }
 
-  const size_t smem = pair ? pair_smem_bytes((int)elem, rmax) : dtb_smem_bytes((int)elem, rmax, rp);
+  const size_t smem = skew ? skew_smem_bytes((int)elem, rmax)
+                           : pair ? pair_smem_bytes((int)elem, rmax) : dtb_smem_bytes((int)elem, rmax, rp);
   const int kmode = pair ? MODE_TILES_PAIR : mode;
   void *fn = dt == J2D_F64 ? kernel_ptr<double>(kmode, r.adjoint) : kernel_ptr<float>(kmode, r.adjoint);
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {

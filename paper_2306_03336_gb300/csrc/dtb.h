@@ -56,6 +56,8 @@ struct DtbState {
 int dtb_rows_max(j2d_dtype dt, size_t smem_optin, int warps);
 // The same for the two-steps-per-sweep tiles (no mailboxes; at most 32 rows).
 int dtb_rows_max_pair(j2d_dtype dt, size_t smem_optin);
+// The same for the skewed tiles (no mailboxes; at most 32 rows).
+int dtb_rows_max_skew(j2d_dtype dt, size_t smem_optin);
 
 DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, size_t smem_optin,
                      const DtbRequest &rq);

@@ -94,7 +94,7 @@ def _weights():
 
 
 NX, NY = 70, 45
-ALGOS = ["onestep", "resident", "bands", "tiles"]
+ALGOS = ["onestep", "resident", "bands", "tiles", "skewed"]
 
 
 @pytest.fixture(scope="module")

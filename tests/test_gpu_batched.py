@@ -20,11 +20,10 @@ def _built():
 SIZES = [(1, 1), (300, 200), (64, 64), (130, 7), (7, 130), (257, 331), (1024, 64), (64, 1024), (95, 95), (513, 2)]
 
 
-def _batch(sizes, dtype, steps, depth, wx, graph=False, replays=1):
-    import torch
+def _batch(sizes, dtype, steps, depth, wx, graph=False, replays=1, algo="tiles"):
     w = np.stack([synth.weights(400 + i) for i in range(len(sizes))])
     us = [synth.field(nx, ny, 500 + i) for i, (nx, ny) in enumerate(sizes)]
-    p = j2d5pt.Plan.batch(sizes, dtype, w).set("algo", "tiles").set("depth", depth).set("tile_wx", wx)
+    p = j2d5pt.Plan.batch(sizes, dtype, w).set("algo", algo).set("depth", depth).set("tile_wx", wx)
     if graph:
         p.set("graph", 1)
     srcs = [p.to_device(u.astype(p.np_dtype), i) for i, u in enumerate(us)]
@@ -39,10 +38,11 @@ def _batch(sizes, dtype, steps, depth, wx, graph=False, replays=1):
     return us, w, outs
 
 
-@pytest.mark.parametrize("depth,wx", [(4, 2), (7, 1), (3, 4)])
-def test_batched_against_oracle(depth, wx):
+@pytest.mark.parametrize("algo,depth,wx", [("tiles", 4, 2), ("tiles", 7, 1), ("tiles", 3, 4), ("skewed", 4, 2),
+                                           ("skewed", 6, 4), ("skewed", 13, 8)])
+def test_batched_against_oracle(algo, depth, wx):
     steps = 13
-    us, w, outs = _batch(SIZES, "f64", steps, depth, wx)
+    us, w, outs = _batch(SIZES, "f64", steps, depth, wx, algo=algo)
     for u, wi, got in zip(us, w, outs):
         assert rel_err(got, oracle.run(u, wi, steps)) <= TOL_F64
 
@@ -59,10 +59,11 @@ def test_batched_bitwise_equal_to_single_grid_onestep():
         p.close()
 
 
-def test_batched_cuda_graph_replay():
+@pytest.mark.parametrize("algo", ["tiles", "skewed"])
+def test_batched_cuda_graph_replay(algo):
     steps = 10
-    _, _, plain = _batch(SIZES, "f64", steps, 4, 2)
-    _, _, graph = _batch(SIZES, "f64", steps, 4, 2, graph=True, replays=3)
+    _, _, plain = _batch(SIZES, "f64", steps, 4, 2, algo=algo)
+    _, _, graph = _batch(SIZES, "f64", steps, 4, 2, graph=True, replays=3, algo=algo)
     for a, b in zip(plain, graph):
         assert np.array_equal(a, b)
 
@@ -121,7 +122,7 @@ def test_single_grid_graph_option():
     p.close()
 
 
-@pytest.mark.parametrize("algo", ["onestep", "resident", "tiles"])
+@pytest.mark.parametrize("algo", ["onestep", "resident", "tiles", "skewed"])
 def test_graph_with_timing(algo):
     """Timing events are not recorded inside the graph capture, so a plan
     with both options runs, replays and reports a kernel time afterwards."""

@@ -72,6 +72,49 @@ def test_random_configuration(i):
         assert rel_err(got, ora) <= f32_bound(steps), c
 
 
+N_SKEWED = 60
+
+
+@pytest.mark.parametrize("i", range(N_SKEWED))
+def test_random_skewed_configuration(i):
+    """The skewed serial tiles on seeded random sizes, depths and tile
+    widths: bit-identical to the one-step kernel and within the oracle bars
+    (forward runs; the schedule is forward only)."""
+    r = np.random.Generator(np.random.PCG64(2306034100 + i))
+    nx = int(r.choice([1, 2, 63, 64, 65, 127, 128, 129, 255, 256, 257, 700]) if r.random() < 0.5 else r.integers(1, 901))
+    ny = int(r.integers(1, 601))
+    steps = int(r.choice([1, 2, 3, 5, 8, 13, 21, 40]))
+    depth = int(r.choice([1, 2, 3, 4, 6, 8, 12, 16, 24, 32]))
+    wx = int(r.choice([1, 2, 4, 8, 16]))
+    dt = str(r.choice(["f64", "f32"]))
+    seed = 2306034200 + i
+    u0 = synth.field(nx, ny, seed)
+    w = synth.weights(seed + 1)
+    p = j2d5pt.Plan(nx, ny, dt, w)
+    src = p.to_device(u0 if dt == "f64" else u0.astype(np.float32))
+    p.set("algo", "onestep")
+    ref_dev = p.empty()
+    p.run(src, ref_dev, steps)
+    p.sync()
+    ref = p.to_host(ref_dev)
+    p.set("algo", "skewed").set("depth", depth).set("tile_wx", wx)
+    out = p.empty()
+    try:
+        p.run(src, out, steps)
+        p.sync()
+    except j2d5pt.J2DError as e:
+        assert e.status == j2d5pt.J2D_ERR_UNSUPPORTED, (nx, ny, steps, depth, wx, dt, str(e))
+        p.close()
+        pytest.skip("refused: %s" % e)
+    got = p.to_host(out)
+    p.close()
+    assert np.array_equal(got, ref), (nx, ny, steps, depth, wx, dt, int(np.count_nonzero(got != ref)))
+    if dt == "f64":
+        assert rel_err(got, oracle.run(u0, w, steps)) <= TOL_F64
+    else:
+        assert rel_err(got, oracle.run_f32(u0.astype(np.float32).astype(np.float64), w, steps)) <= f32_bound(steps)
+
+
 N_BATCHES = 12
 
 
@@ -86,9 +129,10 @@ def test_random_batch(i):
     steps = int(r.choice([1, 4, 9, 17]))
     depth = int(r.choice([1, 2, 4, 8]))
     wx = int(r.choice([1, 2, 4]))
+    algo = "skewed" if i % 3 == 2 else "tiles"
     ws = np.stack([synth.weights(2306033900 + 10 * i + g) for g in range(count)])
     us = [synth.field(nx, ny, 2306034000 + 10 * i + g) for g, (nx, ny) in enumerate(sizes)]
-    p = j2d5pt.Plan.batch(sizes, dt, ws).set("algo", "tiles").set("depth", depth).set("tile_wx", wx)
+    p = j2d5pt.Plan.batch(sizes, dt, ws).set("algo", algo).set("depth", depth).set("tile_wx", wx)
     srcs = [p.to_device(u.astype(p.np_dtype), g) for g, u in enumerate(us)]
     dsts = [p.empty(g) for g in range(count)]
     try:
@@ -105,5 +149,5 @@ def test_random_batch(i):
         a, b = q.to_device(us[g].astype(q.np_dtype)), q.empty()
         q.run(a, b, steps)
         q.sync()
-        assert np.array_equal(outs[g], q.to_host(b)), (i, g, nx, ny, dt, steps, depth, wx)
+        assert np.array_equal(outs[g], q.to_host(b)), (i, g, nx, ny, dt, steps, depth, wx, algo)
         q.close()

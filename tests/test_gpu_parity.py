@@ -15,8 +15,8 @@ from tests.gpu_util import TOL_F64, cell_rel_err, f32_bound, rel_err
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = ["onestep", "resident", "bands", "tiles"]
-DEPTH = {"bands": 3, "tiles": 3}
+ALGOS = ["onestep", "resident", "bands", "tiles", "skewed"]
+DEPTH = {"bands": 3, "tiles": 3, "skewed": 3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -219,7 +219,9 @@ def test_fma_rate_probe():
 
 
 INVARIANCE = [("resident", None, None), ("bands", 1, None), ("bands", 2, None), ("bands", 5, None),
-              ("tiles", 1, 1), ("tiles", 2, 2), ("tiles", 4, 4), ("tiles", 6, 8), ("tiles", 3, 16)]
+              ("tiles", 1, 1), ("tiles", 2, 2), ("tiles", 4, 4), ("tiles", 6, 8), ("tiles", 3, 16),
+              ("skewed", 1, 2), ("skewed", 2, 4), ("skewed", 5, 8), ("skewed", 3, 1), ("skewed", 4, 16),
+              ("skewed", 13, 2), ("skewed", 8, 4)]
 
 
 @pytest.mark.parametrize("algo,depth,wx", INVARIANCE)
