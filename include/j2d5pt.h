@@ -111,6 +111,23 @@ j2d_status j2d5pt_plan(j2d5pt_plan_t *plan, int nx, int ny, j2d_dtype dtype,
 j2d_status j2d5pt_plan_batched(j2d5pt_plan_t *plan, int count, const int *nx, const int *ny,
                                j2d_dtype dtype, const double *weights);
 
+/* Plan for a second stencil shape through the same kernels: the 3x3 box
+ * (j2d9pt), the paper's method applied beyond its j2d5pt case study (title,
+ * Section 1; the step function of Section 3.1 does not depend on the shape):
+ *     out[y][x] = sum over dy, dx in {-1, 0, 1} of weights[3*(dy+1) + (dx+1)] * in[y+dy][x+dx]
+ * i.e. weights row by row from the y-1 row (the row S reads), x-1 first.
+ * Same layout, ring and ownership rules as j2d5pt_plan; host FP64 weights
+ * (rounded to float for J2D_F32), used as given.  The plan runs forward:
+ * j2d5pt_run / j2d5pt_run_host / j2d5pt_autotune and the option, layout,
+ * describe, timing and status calls; its algorithms are J2D_ALGO_ONESTEP and
+ * J2D_ALGO_SKEWED (any other choice runs the skewed tiles).  The adjoint,
+ * weight-gradient and j2d5pt_set_weights calls return J2D_ERR_UNSUPPORTED.
+ * FP64 cells are evaluated as j2d5pt_arith_info describes, with the nine
+ * terms: the FMA chain takes the product of the (y-1, x) term, then the
+ * (y-1, x-1), (y-1, x+1), (y, x), (y, x-1), (y, x+1), (y+1, x), (y+1, x-1),
+ * (y+1, x+1) terms; the integer path the correctly rounded nine-term sum. */
+j2d_status j2d9pt_plan(j2d5pt_plan_t *plan, int nx, int ny, j2d_dtype dtype, const double weights[9]);
+
 j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t plan);
 
 /* Replace the weights {W, E, S, C, N} of grid `index` (host, FP64).  Later
@@ -233,6 +250,9 @@ j2d_status j2d5pt_measure_smem_bandwidth(double *bytes_per_s);
  * independent cell evaluations with register inputs.  With the FMA rate this
  * gives the arithmetic roofline of the FP64 kernels.  Synchronous. */
 j2d_status j2d5pt_measure_exact_rate(double *cells_per_s);
+
+/* The same for the nine-term integer path of the 3x3 box (cells per second). */
+j2d_status j2d9pt_measure_exact_rate(double *cells_per_s);
 
 /* FP64 cell arithmetic (all kernels alike, so results do not depend on the
  * algorithm, depth or tiling).  With J2D_OPT_INT_PATH = 1 (the default), a

@@ -97,7 +97,7 @@ static void drop_graph(j2d5pt_plan_t p) {
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 static j2d_status plan_common(j2d5pt_plan_t *out, int count, const int *nx, const int *ny, j2d_dtype dt,
-                              const double *w) {
+                              const double *w, int shape = 5) {
   if (!out) return fail(J2D_ERR_ARG, "plan: null output pointer");
   *out = nullptr;
   if (dt != J2D_F64 && dt != J2D_F32) return fail(J2D_ERR_ARG, "plan: unknown dtype %d", (int)dt);
@@ -106,8 +106,8 @@ static j2d_status plan_common(j2d5pt_plan_t *out, int count, const int *nx, cons
     if (nx[i] < 1 || ny[i] < 1) return fail(J2D_ERR_ARG, "plan: grid %d has nx=%d ny=%d (need >= 1)", i, nx[i], ny[i]);
     if ((long)nx[i] + 8 > (1L << 30) || (long)ny[i] + 8 > (1L << 30))
       return fail(J2D_ERR_ARG, "plan: grid %d too large", i);
-    for (int d = 0; d < 5; ++d)
-      if (!std::isfinite(w[5 * i + d])) return fail(J2D_ERR_ARG, "plan: grid %d weight %d is not finite", i, d);
+    for (int d = 0; d < shape; ++d)
+      if (!std::isfinite(w[shape * i + d])) return fail(J2D_ERR_ARG, "plan: grid %d weight %d is not finite", i, d);
   }
   auto *p = new j2d5pt_plan_s();
   p->dtype = dt;
@@ -122,7 +122,8 @@ static j2d_status plan_common(j2d5pt_plan_t *out, int count, const int *nx, cons
   long max_partials = 0;
   for (int i = 0; i < count; ++i) {
     GridDesc g = plan_layout(dt, nx[i], ny[i]);
-    for (int d = 0; d < 5; ++d) g.w[d] = dt == J2D_F64 ? w[5 * i + d] : (double)(float)w[5 * i + d];
+    g.shape = shape;
+    for (int d = 0; d < shape; ++d) g.w[d] = dt == J2D_F64 ? w[shape * i + d] : (double)(float)w[shape * i + d];
     p->grids.push_back(g);
     p->ws_off.push_back(ws_bytes);
     ws_bytes += (g.bytes(p->elem) + 255) / 256 * 256;
@@ -155,6 +156,14 @@ extern "C" j2d_status j2d5pt_plan_batched(j2d5pt_plan_t *plan, int count, const 
   return plan_common(plan, count, nx, ny, dtype, weights);
 }
 
+extern "C" j2d_status j2d9pt_plan(j2d5pt_plan_t *plan, int nx, int ny, j2d_dtype dtype, const double weights[9]) {
+  return plan_common(plan, 1, &nx, &ny, dtype, weights, 9);
+}
+
+// The 3x3 box stencil is forward only: its plans refuse the adjoint, the
+// weight gradient and the five-weight setter.
+static bool is_box(j2d5pt_plan_t p) { return p->grids[0].shape == 9; }
+
 extern "C" j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t p) {
   if (!p) return fail(J2D_ERR_ARG, "destroy: null plan");
   if (p->ran && p->last_stream) cudaStreamSynchronize(p->last_stream);
@@ -174,6 +183,7 @@ extern "C" j2d_status j2d5pt_plan_destroy(j2d5pt_plan_t p) {
 
 extern "C" j2d_status j2d5pt_set_weights(j2d5pt_plan_t p, int index, const double *w) {
   if (!p || !w) return fail(J2D_ERR_ARG, "set_weights: null argument");
+  if (is_box(p)) return fail(J2D_ERR_UNSUPPORTED, "set_weights: a 3x3 box plan has nine weights; make a new plan");
   if (index < 0 || index >= (int)p->grids.size()) return fail(J2D_ERR_ARG, "set_weights: index %d out of range", index);
   for (int d = 0; d < 5; ++d)
     if (!std::isfinite(w[d])) return fail(J2D_ERR_ARG, "set_weights: weight %d is not finite", d);
@@ -298,9 +308,10 @@ static const char *algo_name(int a) {
 extern "C" j2d_status j2d5pt_describe(j2d5pt_plan_t p, char *buf, size_t len) {
   if (!p || !buf || len == 0) return fail(J2D_ERR_ARG, "describe: null argument");
   DtbConfig c = resolve(p, 1000, false);
-  snprintf(buf, len, "dtype=%s grids=%zu nx=%d ny=%d pitch=%ld offset=%ld algo=%s depth=%d tile_wx=%d ctas=%d rows=%d sweep=%d sms=%d",
+  snprintf(buf, len, "dtype=%s grids=%zu nx=%d ny=%d pitch=%ld offset=%ld algo=%s depth=%d tile_wx=%d ctas=%d rows=%d sweep=%d sms=%d stencil=%s",
            p->dtype == J2D_F64 ? "f64" : "f32", p->grids.size(), p->grids[0].nx, p->grids[0].ny, p->grids[0].pitch,
-           p->grids[0].off, algo_name(c.algo), c.depth, c.tile_wx, c.ctas, c.rows, c.sweep, p->sms);
+           p->grids[0].off, algo_name(c.algo), c.depth, c.tile_wx, c.ctas, c.rows, c.sweep, p->sms,
+           is_box(p) ? "box9" : "j2d5pt");
   return J2D_OK;
 }
 
@@ -458,6 +469,7 @@ extern "C" j2d_status j2d5pt_run_batched(j2d5pt_plan_t p, const void *const *in,
 
 extern "C" j2d_status j2d5pt_run_adjoint(j2d5pt_plan_t p, const void *lam_T, void *lam_0, long steps, void *stream) {
   if (!p) return fail(J2D_ERR_ARG, "run_adjoint: null plan");
+  if (is_box(p)) return fail(J2D_ERR_UNSUPPORTED, "run_adjoint: the 3x3 box stencil is forward only");
   if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "run_adjoint: batched plans are forward only");
   return run_common(p, &lam_T, &lam_0, steps, true, (cudaStream_t)stream);
 }
@@ -465,6 +477,7 @@ extern "C" j2d_status j2d5pt_run_adjoint(j2d5pt_plan_t p, const void *lam_T, voi
 extern "C" j2d_status j2d5pt_weight_grad(j2d5pt_plan_t p, const void *u_t, const void *lam_t1, double *dw,
                                          void *stream) {
   if (!p || !u_t || !lam_t1 || !dw) return fail(J2D_ERR_ARG, "weight_grad: null argument");
+  if (is_box(p)) return fail(J2D_ERR_UNSUPPORTED, "weight_grad: the 3x3 box stencil is forward only");
   if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "weight_grad: batched plans are forward only");
   if (!aligned16(u_t) || !aligned16(lam_t1)) return fail(J2D_ERR_ALIGN, "weight_grad: buffer not 16-byte aligned");
   if (((uintptr_t)dw & 7u) != 0) return fail(J2D_ERR_ALIGN, "weight_grad: dw not 8-byte aligned");
@@ -479,6 +492,7 @@ extern "C" j2d_status j2d5pt_weight_grad(j2d5pt_plan_t p, const void *u_t, const
 extern "C" j2d_status j2d5pt_adjoint_step_wgrad(j2d5pt_plan_t p, const void *u_t, const void *lam_t1, void *lam_t,
                                                double *dw, void *stream) {
   if (!p || !u_t || !lam_t1 || !lam_t || !dw) return fail(J2D_ERR_ARG, "adjoint_step_wgrad: null argument");
+  if (is_box(p)) return fail(J2D_ERR_UNSUPPORTED, "adjoint_step_wgrad: the 3x3 box stencil is forward only");
   if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "adjoint_step_wgrad: batched plans are forward only");
   if (lam_t == lam_t1 || lam_t == u_t) return fail(J2D_ERR_ARG, "adjoint_step_wgrad: lam_t aliases an input");
   if (!aligned16(u_t) || !aligned16(lam_t1) || !aligned16(lam_t))
@@ -554,7 +568,7 @@ static std::string tune_key(j2d5pt_plan_t p, long steps) {
     h = (h ^ (unsigned long long)g.ny) * 1099511628211ull;
   }
   k += "|" + std::to_string(p->grids.size()) + "|" + std::to_string(h) + "|ip" + std::to_string(int_path_of(p)) +
-       "|sw" + std::to_string(p->opt_sweep_steps);
+       "|sw" + std::to_string(p->opt_sweep_steps) + "|s" + std::to_string(p->grids[0].shape);
   long b = 1;
   while (b < steps) b <<= 1;
   k += "|" + std::to_string(b);
@@ -615,10 +629,12 @@ static j2d_status autotune_common(j2d5pt_plan_t p, const void *const *in, void *
       cands.push_back({J2D_ALGO_RESIDENT, 0, 0});
   }
   const int depths[] = {2, 4, 6, 8, 12, 16, 24, 32};
+  const bool box = is_box(p);  // the box runs the one-step kernel or the skewed tiles
   for (int d : depths) {
     if (d > steps) break;
-    if (single) cands.push_back({J2D_ALGO_BANDS, d, 0});
-    for (int wx : {1, 2, 4}) cands.push_back({J2D_ALGO_TILES, d, wx});
+    if (single && !box) cands.push_back({J2D_ALGO_BANDS, d, 0});
+    if (!box)
+      for (int wx : {1, 2, 4}) cands.push_back({J2D_ALGO_TILES, d, wx});
     for (int wx : {2, 4, 8}) cands.push_back({J2D_ALGO_SKEWED, d, wx});
   }
   float best_ms = 1e30f;
@@ -703,6 +719,13 @@ extern "C" j2d_status j2d5pt_measure_exact_rate(double *cells_per_s) {
   if (!cells_per_s) return fail(J2D_ERR_ARG, "measure_exact_rate: null pointer");
   cudaError_t e = measure_exact(cells_per_s);
   if (e != cudaSuccess) return cuda_fail(e, "measure_exact_rate");
+  return J2D_OK;
+}
+
+extern "C" j2d_status j2d9pt_measure_exact_rate(double *cells_per_s) {
+  if (!cells_per_s) return fail(J2D_ERR_ARG, "j2d9pt_measure_exact_rate: null pointer");
+  cudaError_t e = measure_exact_box(cells_per_s);
+  if (e != cudaSuccess) return cuda_fail(e, "j2d9pt_measure_exact_rate");
   return J2D_OK;
 }
 

@@ -78,24 +78,30 @@ __device__ __forceinline__ T stencil(const Links<T> &a, T xm, T xp, T ym, T c, T
 constexpr unsigned kExactMask = 0x0F;
 constexpr int kExactGuard = 11;
 
-struct ExactW {
-  uint64_t m[5];  // significands with the implicit bit, order xm, xp, ym, c, yp
-  int e[5];       // biased exponents
-  bool ok;        // all five positive normal
+// Weight significands and exponents of an NT-term cell for the integer path.
+template <int NT> struct ExactWN {
+  uint64_t m[NT];  // significands with the implicit bit, in the cell's term order
+  int e[NT];       // biased exponents
+  bool ok;         // all NT positive normal
 };
+using ExactW = ExactWN<5>;  // the five-point cell: order xm, xp, ym, c, yp
 
-__device__ __forceinline__ ExactW exact_weights(const Links<double> &a) {
-  const double w[5] = {a.xm, a.xp, a.ym, a.c, a.yp};
-  ExactW u;
+template <int NT> __device__ __forceinline__ ExactWN<NT> exact_weights_n(const double (&w)[NT]) {
+  ExactWN<NT> u;
   u.ok = true;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < NT; ++i) {
     const uint64_t b = (uint64_t)__double_as_longlong(w[i]);
     u.e[i] = (int)(b >> 52);  // includes the sign bit: negative weights fail the range test
     u.ok &= (unsigned)(u.e[i] - 1) < 2046u;
     u.m[i] = (b & ((1ull << 52) - 1)) | (1ull << 52);
   }
   return u;
+}
+
+__device__ __forceinline__ ExactW exact_weights(const Links<double> &a) {
+  const double w[5] = {a.xm, a.xp, a.ym, a.c, a.yp};
+  return exact_weights_n<5>(w);
 }
 
 // Four-word (128-bit) add with carry: a += b.
@@ -108,19 +114,21 @@ __device__ __forceinline__ void add128(uint32_t (&a)[4], uint32_t b0, uint32_t b
       : "r"(b0), "r"(b1), "r"(b2), "r"(b3));
 }
 
-// Correctly rounded xm*W + xp*E + ym*S + c*C + yp*N on the fast path; returns
-// false (r untouched) when the fast path does not apply.  Significands are
-// split into 32-bit words (high word 21 bits with the implicit bit); a
-// product of the shifted value significand (two words) and the weight
-// significand is four 32x32->64 multiplies; the frame is four 32-bit words.
-__device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double xp, double ym, double c, double yp,
-                                              double &r) {
-  const double v[5] = {xm, xp, ym, c, yp};
-  uint32_t m0[5], m1[5];
-  int E[5];
+// Correctly rounded sum of the NT products w[i] * v[i] on the fast path;
+// returns false (r untouched) when the fast path does not apply.
+// Significands are split into 32-bit words (high word 21 bits with the
+// implicit bit); a product of the shifted value significand (two words) and
+// the weight significand is four 32x32->64 multiplies; the frame is four
+// 32-bit words.  Each term is below 2^(64+53) = 2^117, so up to 2^11 terms
+// fit the 128-bit frame without loss (NT = 5: the frame stays below 2^120;
+// NT = 9: below 2^121).
+template <int NT>
+__device__ __forceinline__ bool stencil_exact_n(const ExactWN<NT> &u, const double (&v)[NT], double &r) {
+  uint32_t m0[NT], m1[NT];
+  int E[NT];
   bool ok = true;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < NT; ++i) {
     const uint32_t hi = (uint32_t)__double2hiint(v[i]);
     m0[i] = (uint32_t)__double2loint(v[i]);
     const int e = (int)(hi >> 20);  // includes the sign bit: negative values fail the range test
@@ -128,11 +136,13 @@ __device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double
     m1[i] = (hi & 0xFFFFFu) | 0x100000u;
     E[i] = e + u.e[i];  // product i = p_i * 2^(E[i] - 2150), p_i in [2^104, 2^106)
   }
-  const int Em = max(max(max(E[0], E[1]), max(E[2], E[3])), E[4]);
+  int Em = E[0];
+#pragma unroll
+  for (int i = 1; i < NT; ++i) Em = max(Em, E[i]);
   uint32_t f[4] = {0u, 0u, 0u, 0u};
   int sall = 0;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < NT; ++i) {
     const int s = kExactGuard - (Em - E[i]);  // frame position: p_i * 2^s, s <= kExactGuard
     sall |= s;                               // any s < 0 leaves the fast path
     const uint32_t a0 = m0[i] << (s & 31), a1 = __funnelshift_l(m0[i], m1[i], s);  // value significand * 2^s
@@ -144,8 +154,8 @@ __device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double
     add128(f, (uint32_t)p00, (uint32_t)p10, (uint32_t)p11, (uint32_t)(p11 >> 32));
   }
   ok &= sall >= 0;
-  // frame F = f[3]:f[2]:f[1]:f[0] = sum * 2^(2150 + kExactGuard - Em), F in [2^115, 2^120)
-  const int z = __clz((int)f[3]) & 31;  // 8..12 on the fast path
+  // frame F = f[3]:f[2]:f[1]:f[0] = sum * 2^(2150 + kExactGuard - Em), F in [2^115, 2^121)
+  const int z = __clz((int)f[3]) & 31;  // 7..12 on the fast path
   const uint32_t g3 = __funnelshift_l(f[2], f[3], z), g2 = __funnelshift_l(f[1], f[2], z);
   const uint32_t g1 = __funnelshift_l(f[0], f[1], z), g0 = f[0] << z;
   uint64_t kept = ((uint64_t)g3 << 21) | (g2 >> 11);  // the top 53 bits
@@ -158,6 +168,13 @@ __device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double
   ok &= (unsigned)(e - 1) < 2046u;
   if (ok) r = __longlong_as_double((long long)(((uint64_t)(e - 1) << 52) + kept));
   return ok;
+}
+
+// The five-point cell: xm*W + xp*E + ym*S + c*C + yp*N.
+__device__ __forceinline__ bool stencil_exact(const ExactW &u, double xm, double xp, double ym, double c, double yp,
+                                              double &r) {
+  const double v[5] = {xm, xp, ym, c, yp};
+  return stencil_exact_n<5>(u, v, r);
 }
 
 // Whether cell (x, y) takes the integer path (logical coordinates) in a run
@@ -174,6 +191,53 @@ __device__ __forceinline__ double stencil_cell(const Links<double> &a, const Exa
   if (exact && u.ok && stencil_exact(u, xm, xp, ym, c, yp, r)) return r;
   return stencil(a, xm, xp, ym, c, yp);
 }
+
+// ---- the 3x3 box stencil (j2d9pt) --------------------------------------------
+// A second stencil shape through the same kernels.  Weights come in the
+// user's order (rows y-1, y, y+1, columns x-1, x, x+1); every box kernel
+// evaluates a cell as the product of the (y-1, x) term, then fused
+// multiply-adds of (y-1, x-1), (y-1, x+1), (y, x), (y, x-1), (y, x+1),
+// (y+1, x), (y+1, x-1), (y+1, x+1): the operands of the row a sweep loads
+// last enter last.  Box9 holds the weights in that chain order.
+template <typename T> struct Box9 { T w[9]; };
+
+// The chain over three rows (m: y-1, c: y, p: y+1), each as (x-1, x, x+1).
+template <typename T>
+__device__ __forceinline__ T stencil_box(const Box9<T> &b, T m0, T m1, T m2, T c0, T c1, T c2, T p0, T p1, T p2) {
+  T r = mul_rn(b.w[0], m1);
+  r = fma_rn(b.w[1], m0, r);
+  r = fma_rn(b.w[2], m2, r);
+  r = fma_rn(b.w[3], c1, r);
+  r = fma_rn(b.w[4], c0, r);
+  r = fma_rn(b.w[5], c2, r);
+  r = fma_rn(b.w[6], p1, r);
+  r = fma_rn(b.w[7], p0, r);
+  r = fma_rn(b.w[8], p2, r);
+  return r;
+}
+
+// FP64: the integer path on the cells exact_cell() selects, else the chain.
+__device__ __forceinline__ double stencil_box_cell(const Box9<double> &b, const ExactWN<9> &u, bool exact,
+                                                   double m0, double m1, double m2, double c0, double c1, double c2,
+                                                   double p0, double p1, double p2) {
+  double r;
+  if (exact && u.ok) {
+    const double v[9] = {m1, m0, m2, c1, c0, c2, p1, p0, p2};  // chain order, as the weights
+    if (stencil_exact_n<9>(u, v, r)) return r;
+  }
+  return stencil_box(b, m0, m1, m2, c0, c1, c2, p0, p1, p2);
+}
+__device__ __forceinline__ float stencil_box_cell(const Box9<float> &b, const ExactWN<9> &, bool, float m0, float m1,
+                                                  float m2, float c0, float c1, float c2, float p0, float p1,
+                                                  float p2) {
+  return stencil_box(b, m0, m1, m2, c0, c1, c2, p0, p1, p2);
+}
+
+// Box weights in chain order from the user's order.
+template <typename T> __host__ __device__ inline Box9<T> box_chain(const double *w) {
+  return Box9<T>{{(T)w[1], (T)w[0], (T)w[2], (T)w[4], (T)w[3], (T)w[5], (T)w[7], (T)w[6], (T)w[8]}};
+}
+__device__ __forceinline__ ExactWN<9> box_exact_weights(const Box9<double> &b) { return exact_weights_n<9>(b.w); }
 
 // Link weights of logical cell (x, y) of an nx*ny grid with a one-cell ring.
 // Forward: interior cells use W, E, S, C, N; ring and outside cells keep their

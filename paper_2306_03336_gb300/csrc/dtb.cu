@@ -77,9 +77,9 @@ constexpr int kSkewInts = 10;
 
 // Per-grid data the kernel reads from global memory.
 struct GridDev {
-  int nx, ny, off, pad;
+  int nx, ny, off, shape;
   long pitch;
-  double w[5];
+  double w[9];  // {W, E, S, C, N}, or the nine box weights in row order
   void *buf[3];  // 0 = in, 1 = workspace, 2 = out
 };
 
@@ -1034,9 +1034,77 @@ __device__ __forceinline__ void sweep_skew(T *drow, const T *hct, int rows, int 
   }
 }
 
+// The same step for the 3x3 box: every row's x-1 / x+1 neighbours enter
+// (shuffles; lane 0 and lane 31 take the halo column, hct[j] = strip row j-2).
+template <typename T, bool DEAD>
+__device__ __forceinline__ void sweep_skew_box(T *drow, const T *hct, int rows, int r_lo, int r_hi, int lane,
+                                               const Box9<T> &b, const ExactWN<9> &u, bool ip, int xl, int yb,
+                                               const T (&ta)[VecOf<T>::V], const T (&tb)[VecOf<T>::V],
+                                               uint32_t dead) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  T ra[V], rb[V], rc[V], o[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    ra[e] = ta[e];
+    rb[e] = tb[e];
+  }
+  auto sides = [&](const T (&row)[V], T h, T &l, T &r) {
+    l = __shfl_up_sync(0xffffffffu, row[V - 1], 1);
+    r = __shfl_down_sync(0xffffffffu, row[0], 1);
+    if (lane == 0) l = h;
+    if (lane == 31) r = h;
+  };
+  T al, ar, bl, br, cl, cr;
+  sides(ra, hct[0], al, ar);
+  sides(rb, hct[1], bl, br);
+  auto shift = [&]() {
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      ra[e] = rb[e];
+      rb[e] = rc[e];
+    }
+    al = bl;
+    ar = br;
+    bl = cl;
+    br = cr;
+  };
+  int r = 0;
+  for (; r < r_lo; ++r) {
+    vload(drow + r * SW, false, rc);
+    sides(rc, hct[r + 2], cl, cr);
+    vstore(drow + r * SW, rb);
+    shift();
+  }
+  for (; r < r_hi; ++r) {
+    vload(drow + r * SW, false, rc);
+    sides(rc, hct[r + 2], cl, cr);
+    const int y = yb + r;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const T m0 = e == 0 ? al : ra[e - 1], m2 = e == V - 1 ? ar : ra[e + 1];
+      const T c0 = e == 0 ? bl : rb[e - 1], c2 = e == V - 1 ? br : rb[e + 1];
+      const T p0 = e == 0 ? cl : rc[e - 1], p2 = e == V - 1 ? cr : rc[e + 1];
+      o[e] = stencil_box_cell(b, u, exact_cell(xl + e, y, ip), m0, ra[e], m2, c0, rb[e], c2, p0, rc[e], p2);
+      if (DEAD && (dead & (1u << e))) o[e] = rb[e];
+    }
+    vstore(drow + r * SW, o);
+    shift();
+  }
+  for (; r < rows; ++r) {
+    vload(drow + r * SW, false, rc);
+    vstore(drow + r * SW, rb);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      ra[e] = rb[e];
+      rb[e] = rc[e];
+    }
+  }
+}
+
 // Advance this warp's strip of one skewed tile (job) by k levels: load level
 // 0, k steps, store level k.  Called by every warp of the CTA with the same k.
-template <typename T>
+template <typename T, int NP>
 __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, int warp, int src, int dst, int k,
                                int par, uint32_t &mbar_phase, const Prefetch &pf) {
   constexpr int V = VecOf<T>::V;
@@ -1046,7 +1114,11 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
   const int region = skew_region_elems((int)sizeof(T), R);
   T *wbase = reinterpret_cast<T *>(smem + kHeaderBytes);
   T *data = wbase + (size_t)warp * region;
-  T *hc = data + (size_t)R * SW;  // [2][32]: entry r = halo column x-1 (then x+SW) at strip row r-1
+  // [2][32]: halo column x-1 (then x+SW), entry j = strip row j - H0 (the
+  // five-point cell reads the centre row's neighbours, rows -1 .. R-2; the
+  // box cell all three rows', rows -2 .. R-1)
+  T *hc = data + (size_t)R * SW;
+  constexpr int H0 = NP == 9 ? 2 : 1;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   const int g = job[0], tx0 = job[1], vx0 = job[2], vx1 = job[3], q0 = job[4], nq = job[5], v0 = job[6],
             v1 = job[7];
@@ -1067,7 +1139,14 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
   const CUtensorMap *map_store = kp.maps + (size_t)g * 6 + 3 + dst;
   const Links<T> a{(T)gd.w[0], (T)gd.w[1], (T)gd.w[2], (T)gd.w[3], (T)gd.w[4]};
   ExactW u{};
-  if constexpr (std::is_same<T, double>::value) u = exact_weights(a);
+  Box9<T> b9{};
+  ExactWN<9> u9{};
+  if constexpr (NP == 9) {
+    b9 = box_chain<T>(gd.w);
+    if constexpr (std::is_same<T, double>::value) u9 = box_exact_weights(b9);
+  } else {
+    if constexpr (std::is_same<T, double>::value) u = exact_weights(a);
+  }
   const bool ip = kp.int_path != 0;
   // neighbours in the tile (the strip above is full whenever this one has rows)
   const int wT = wy > 0 ? warp - WX : -1;
@@ -1107,9 +1186,9 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
       t2c[e] = wT < 0 ? gval(y0 - 2, xl + e) : T(0);
       t1c[e] = wT < 0 ? gval(y0 - 1, xl + e) : T(0);
     }
-    if (lane == 0) {
-      cl0 = gval(y0 - 1, x0 - 1);
-      cr0 = gval(y0 - 1, x0 + SW);
+    if (lane < H0) {  // the corner cells of halo rows -H0 .. -1, one per lane
+      cl0 = gval(y0 - H0 + lane, x0 - 1);
+      cr0 = gval(y0 - H0 + lane, x0 + SW);
     }
     wait_mbar(&bars[warp], mbar_phase, kp);
     mbar_phase ^= 1u;
@@ -1130,8 +1209,8 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
     pb[e] = t1c[e];
   }
   T pcl = cl0, pcr = cr0;
-  T phl = x0 == 1 ? gval(y0 + lane - 1, 0) : T(0);
-  T phr = x0 + SW == nx + 1 ? gval(y0 + lane - 1, nx + 1) : T(0);
+  T phl = x0 == 1 ? gval(y0 + lane - H0, 0) : T(0);
+  T phr = x0 + SW == nx + 1 ? gval(y0 + lane - H0, nx + 1) : T(0);
   for (int L = 1; L <= k; ++L) {
     T ta[V], tb[V];  // rows -2 and -1 at level L-1
     if (act) {
@@ -1146,14 +1225,19 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
           tb[e] = pb[e];
         }
       }
-      if (lane < rows) {
-        // halo columns at strip row lane-1 (level L-1; the ring columns
-        // at the physical row y0 + lane - L, loaded ahead)
+      if (lane < rows + 2 * (H0 - 1)) {
+        // halo columns at strip row lane - H0 (level L-1; the ring columns
+        // at the physical row y0 + lane - H0 - (L-1), loaded ahead)
+        const int row = lane - H0;
         T hl, hr;
-        if (wL >= 0) hl = lane > 0 ? nbdata(wL)[(lane - 1) * SW + SW - 1] : wTL >= 0 ? nbdata(wTL)[(R - 1) * SW + SW - 1] : pcl;
-        else hl = phl;  // the ring column, or zero at a band edge (overlapped halo)
-        if (wR >= 0) hr = lane > 0 ? nbdata(wR)[(lane - 1) * SW] : wTR >= 0 ? nbdata(wTR)[(R - 1) * SW] : pcr;
-        else hr = phr;
+        if (wL >= 0)
+          hl = row >= 0 ? nbdata(wL)[row * SW + SW - 1] : wTL >= 0 ? nbdata(wTL)[(R + row) * SW + SW - 1] : pcl;
+        else
+          hl = phl;  // the ring column, or zero at a band edge (overlapped halo)
+        if (wR >= 0)
+          hr = row >= 0 ? nbdata(wR)[row * SW] : wTR >= 0 ? nbdata(wTR)[(R + row) * SW] : pcr;
+        else
+          hr = phr;
         hc[lane] = hl;
         hc[32 + lane] = hr;
       }
@@ -1165,20 +1249,27 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
         if (wT < 0 && !first) {
           vload(sb(par ^ 1, L, 0) + (x0 - tx0) + lane * V, false, pa);
           vload(sb(par ^ 1, L, 1) + (x0 - tx0) + lane * V, false, pb);
-          if (lane == 0) {
-            if (wL >= 0) pcl = sb(par ^ 1, L, 1)[x0 - 1 - tx0];
-            if (wR >= 0) pcr = sb(par ^ 1, L, 1)[x0 + SW - tx0];
+          if (lane < H0) {
+            if (wL >= 0) pcl = sb(par ^ 1, L, 2 - H0 + lane)[x0 - 1 - tx0];
+            if (wR >= 0) pcr = sb(par ^ 1, L, 2 - H0 + lane)[x0 + SW - tx0];
           }
         }
-        if (x0 == 1) phl = gval(y0 + lane - L - 1, 0);
-        if (x0 + SW == nx + 1) phr = gval(y0 + lane - L - 1, nx + 1);
+        if (x0 == 1) phl = gval(y0 + lane - L - H0, 0);
+        if (x0 + SW == nx + 1) phr = gval(y0 + lane - L - H0, nx + 1);
       }
       // rows whose physical row y0 + r - L is interior take the stencil, the rest the identity
       const int r_lo = min(max(L + 1 - y0, 0), rows), r_hi = max(min(ny + L + 1 - y0, rows), r_lo);
-      if (any_dead)
-        sweep_skew<T, true>(drow, hct, rows, r_lo, r_hi, lane, a, u, ip, xl, y0 - L, ta, tb, dead);
-      else
-        sweep_skew<T, false>(drow, hct, rows, r_lo, r_hi, lane, a, u, ip, xl, y0 - L, ta, tb, dead);
+      if constexpr (NP == 9) {
+        if (any_dead)
+          sweep_skew_box<T, true>(drow, hct, rows, r_lo, r_hi, lane, b9, u9, ip, xl, y0 - L, ta, tb, dead);
+        else
+          sweep_skew_box<T, false>(drow, hct, rows, r_lo, r_hi, lane, b9, u9, ip, xl, y0 - L, ta, tb, dead);
+      } else {
+        if (any_dead)
+          sweep_skew<T, true>(drow, hct, rows, r_lo, r_hi, lane, a, u, ip, xl, y0 - L, ta, tb, dead);
+        else
+          sweep_skew<T, false>(drow, hct, rows, r_lo, r_hi, lane, a, u, ip, xl, y0 - L, ta, tb, dead);
+      }
       if (bottom && L < k) {
         __syncwarp();
         T v[V];
@@ -1344,7 +1435,7 @@ __global__ void ring_copy_grids_kernel(const GridDev *grids, int copy_ws, int co
   }
 }
 
-template <typename T, bool ADJ, int MODE>
+template <typename T, bool ADJ, int MODE, int NP = 5>
 __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant__ KParams kp) {
   constexpr int SWc = 32 * VecOf<T>::V;
   extern __shared__ __align__(1024) char smem[];
@@ -1384,7 +1475,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
             pf.y = nj[4] + wy * kp.rmax;
           }
         }
-        run_strip_skew<T>(kp, job, smem, warp, src, dst, k, par, phase, pf);
+        run_strip_skew<T, NP>(kp, job, smem, warp, src, dst, k, par, phase, pf);
       }
       if (lane == 0) {
         bulk_wait_all();
@@ -1520,6 +1611,8 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
   if (algo == J2D_ALGO_BANDS && !single) algo = J2D_ALGO_TILES;
   if (algo == J2D_ALGO_SKEWED && rq.adjoint) algo = J2D_ALGO_TILES;  // the skewed order is forward only
+  // the 3x3 box runs the one-step kernel or the skewed tiles
+  if (grids[0].shape == 9 && algo != J2D_ALGO_ONESTEP) algo = J2D_ALGO_SKEWED;
   c.algo = algo;
   c.depth = rq.depth > 0 ? rq.depth : (dt == J2D_F64 ? 4 : 8);
   c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : (dt == J2D_F64 ? 4 : 2);
@@ -1620,11 +1713,11 @@ static void ensure(void *&p, size_t &cap, size_t need, cudaError_t &err) {
 }
 
 template <typename T>
-static void *kernel_ptr(int mode, bool adj) {
+static void *kernel_ptr(int mode, bool adj, int np) {
   if constexpr (std::is_same<T, float>::value) {
     if (mode == MODE_TILES_PAIR) return (void *)dtb_kernel<float, false, MODE_TILES_PAIR>;
   }
-  if (mode == MODE_SKEW) return (void *)dtb_kernel<T, false, MODE_SKEW>;
+  if (mode == MODE_SKEW) return np == 9 ? (void *)dtb_kernel<T, false, MODE_SKEW, 9> : (void *)dtb_kernel<T, false, MODE_SKEW>;
   if (mode == MODE_BANDS) return adj ? (void *)dtb_kernel<T, true, MODE_BANDS> : (void *)dtb_kernel<T, false, MODE_BANDS>;
   return adj ? (void *)dtb_kernel<T, true, MODE_TILES> : (void *)dtb_kernel<T, false, MODE_TILES>;
 }
@@ -1639,6 +1732,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   const bool pair = r.cfg.sweep == 2 && dt == J2D_F32 && r.cfg.algo == J2D_ALGO_TILES && !r.adjoint;
   const bool skew = r.cfg.algo == J2D_ALGO_SKEWED;
   if (skew && r.adjoint) { err = "the skewed schedule is forward only"; return cudaErrorNotSupported; }
+  if (grids[0].shape == 9 && (!skew || r.adjoint)) { err = "the box stencil runs the skewed schedule"; return cudaErrorNotSupported; }
   const int rmax = skew ? dtb_rows_max_skew(dt, r.smem_optin)
                         : pair ? dtb_rows_max_pair(dt, r.smem_optin) : dtb_rows_max(dt, r.smem_optin, kWarps);
   const int rp = (rmax + 3) / 4 * 4;
@@ -1884,7 +1978,8 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
     hg[i].ny = g.ny;
     hg[i].off = (int)g.off;
     hg[i].pitch = g.pitch;
-    for (int d = 0; d < 5; ++d) hg[i].w[d] = g.w[d];
+    hg[i].shape = g.shape;
+    for (int d = 0; d < 9; ++d) hg[i].w[d] = g.w[d];
     hg[i].buf[0] = const_cast<void *>(r.in[i]);
     hg[i].buf[1] = r.ws[i];
     hg[i].buf[2] = r.out[i];
@@ -1981,7 +2076,8 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   const size_t smem = skew ? skew_smem_bytes((int)elem, rmax)
                            : pair ? pair_smem_bytes((int)elem, rmax) : dtb_smem_bytes((int)elem, rmax, rp);
   const int kmode = pair ? MODE_TILES_PAIR : mode;
-  void *fn = dt == J2D_F64 ? kernel_ptr<double>(kmode, r.adjoint) : kernel_ptr<float>(kmode, r.adjoint);
+  void *fn = dt == J2D_F64 ? kernel_ptr<double>(kmode, r.adjoint, grids[0].shape)
+                           : kernel_ptr<float>(kmode, r.adjoint, grids[0].shape);
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
     err = "shared memory attribute";
     return e;

@@ -17,7 +17,8 @@ struct GridDesc {
   int nx = 0, ny = 0;
   long pitch = 0;  // elements per row
   long off = 0;    // element offset of logical column 0
-  double w[5] = {0, 0, 0, 0, 0};
+  int shape = 5;   // 5: the five-point stencil, w = {W, E, S, C, N}; 9: the 3x3 box, w in row order
+  double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   size_t bytes(size_t elem) const { return (size_t)(ny + 2) * (size_t)pitch * elem; }
 };
 
@@ -67,6 +68,7 @@ cudaError_t launch_adjoint_wgrad(j2d_dtype dt, const void *u, const void *lam1, 
                                  double *partials, long max_partials, const GridDesc &g, int ipath, cudaStream_t s);
 cudaError_t measure_fma(j2d_dtype dt, double *rate);
 cudaError_t measure_exact(double *rate);
+cudaError_t measure_exact_box(double *rate);
 cudaError_t measure_smem(double *bytes_per_s);
 
 }  // namespace j2d

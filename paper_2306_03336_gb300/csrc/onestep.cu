@@ -177,6 +177,76 @@ __global__ void __launch_bounds__(256) onestep_kernel(const T *__restrict__ in, 
   if constexpr (WG) block_partials(acc, partials);
 }
 
+// One step of the 3x3 box stencil (j2d9pt), the same layout as
+// onestep_kernel: a warp takes a 32-vector column strip of ROWS rows,
+// holding ROWS+2 rows in registers; every row's x-1 / x+1 neighbours come
+// from the adjacent lane by shuffles (lanes 0 and 31 read the one value
+// beyond the warp).  Ring and outside cells keep their value.
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(256) onestep_box_kernel(const T *__restrict__ in, T *__restrict__ out, long pitch,
+                                                          int off, int nx, int ny, Box9<T> b, int ipath) {
+  constexpr int V = VecOf<T>::V;
+  using VT = typename VecOf<T>::type;
+  const int lane = threadIdx.x;
+  const int H = ny + 2;
+  const long ncs = (pitch + 32 * V - 1) / (32 * V);
+  const long nitems = ncs * ((H + ROWS - 1) / ROWS);
+  const long nwarps = (long)gridDim.x * kWarpsX;
+  ExactWN<9> u{};
+  if constexpr (std::is_same<T, double>::value) u = box_exact_weights(b);
+  for (long it = (long)blockIdx.x * kWarpsX + threadIdx.y; it < nitems; it += nwarps) {
+    const long pc0 = ((it % ncs) * 32 + lane) * V;
+    const bool live = pc0 < pitch;
+    const int xl0 = (int)(pc0 - off);  // logical x of element 0
+    const int y0 = (int)(it / ncs) * ROWS;
+    const bool lval = live && (xl0 - 1 >= 0) && (xl0 - 1 <= nx + 1);
+    const bool rval = live && (xl0 + V <= nx + 1);
+    // rows y0-1 .. y0+ROWS with their left / right neighbours
+    T t[ROWS + 2][V], tl[ROWS + 2], tr[ROWS + 2];
+#pragma unroll
+    for (int r = 0; r < ROWS + 2; ++r) {
+      const int y = y0 - 1 + r;
+      const bool yin = y >= 0 && y < H;
+      if (live && yin) {
+        unpack<T, V>(*reinterpret_cast<const VT *>(in + (long)y * pitch + pc0), t[r]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) t[r][v] = T(0);
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int x = xl0 + v;
+        if (x < 0 || x > nx + 1) t[r][v] = T(0);  // row padding reads as zero
+      }
+      tl[r] = __shfl_up_sync(0xffffffffu, t[r][V - 1], 1);
+      tr[r] = __shfl_down_sync(0xffffffffu, t[r][0], 1);
+      if (lane == 0) tl[r] = (lval && yin) ? in[(long)y * pitch + pc0 - 1] : T(0);
+      if (lane == 31) tr[r] = (rval && yin) ? in[(long)y * pitch + pc0 + V] : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const int y = y0 + r;
+      if (y >= H) break;
+      T o[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int x = xl0 + v;
+        if (y >= 1 && y <= ny && x >= 1 && x <= nx) {
+          auto nb = [&](int rr, int d) -> T {
+            const int e = v + d;
+            return e < 0 ? tl[rr] : e >= V ? tr[rr] : t[rr][e];
+          };
+          o[v] = stencil_box_cell(b, u, exact_cell(x, y, ipath != 0), nb(r, -1), nb(r, 0), nb(r, 1), nb(r + 1, -1),
+                                  nb(r + 1, 0), nb(r + 1, 1), nb(r + 2, -1), nb(r + 2, 0), nb(r + 2, 1));
+        } else {
+          o[v] = t[r + 1][v];  // ring and outside cells keep their value
+        }
+      }
+      if (live) *reinterpret_cast<VT *>(out + (long)y * pitch + pc0) = pack(o, (VT *)nullptr);
+    }
+  }
+}
+
 // Copy the ring (rows 0 and ny+1, columns 0 and nx+1) of `in` to `out`.
 template <typename T>
 __global__ void ring_copy_kernel(const T *__restrict__ in, T *__restrict__ out, long pitch, int off, int nx,
@@ -331,6 +401,26 @@ __global__ void exact_rate_kernel(double *out, int iters, ExactW u, Links<double
   out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+// The same probe for the 9-term integer path of the 3x3 box.
+__global__ void exact_rate_box_kernel(double *out, int iters, ExactWN<9> u, Box9<double> b) {
+  double s[2][9];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s[j][i] = 0.05 + 0.03 * (j * 9 + i) + threadIdx.x * 1e-6;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double o = stencil_box_cell(b, u, true, s[j][0], s[j][1], s[j][2], s[j][3], s[j][4], s[j][5], s[j][6],
+                                        s[j][7], s[j][8]);
+#pragma unroll
+      for (int i = 8; i > 0; --i) s[j][i] = s[j][i - 1];
+      s[j][0] = o;
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s[0][0] + s[1][0];
+}
+
 // ---- host launchers --------------------------------------------------------
 
 template <typename T>
@@ -344,6 +434,8 @@ constexpr int kOneRows = 8;       // rows per work item, FP64 (arithmetic bound:
 constexpr int kOneRowsF32 = 16;   // FP32 (HBM bound): more rows, fewer halo re-reads
 constexpr int kWgradRows = 32;    // rows per thread of the weight gradient (streamed): amortises the reduction
 constexpr int kOneRowsWG = 4;     // rows per work item of the fused adjoint step + weight gradient (registers)
+constexpr int kBoxRows = 4;       // rows per work item of the one-step box kernel, FP64 (registers)
+constexpr int kBoxRowsF32 = 8;    // the same, FP32
 
 std::atomic<long> g_launches{0};
 
@@ -374,6 +466,18 @@ cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, co
                            cudaStream_t s) {
   note_launch();
   const dim3 blk(32, kWarpsX);
+  if (g.shape == 9) {  // the 3x3 box: forward only
+    if (dt == J2D_F64) {
+      const dim3 grd = persistent_grid(onestep_box_kernel<double, kBoxRows>, g, 2, kBoxRows);
+      onestep_box_kernel<double, kBoxRows><<<grd, blk, 0, s>>>((const double *)in, (double *)out, g.pitch,
+                                                               (int)g.off, g.nx, g.ny, box_chain<double>(g.w), ipath);
+    } else {
+      const dim3 grd = persistent_grid(onestep_box_kernel<float, kBoxRowsF32>, g, 4, kBoxRowsF32);
+      onestep_box_kernel<float, kBoxRowsF32><<<grd, blk, 0, s>>>((const float *)in, (float *)out, g.pitch,
+                                                                 (int)g.off, g.nx, g.ny, box_chain<float>(g.w), 0);
+    }
+    return cudaGetLastError();
+  }
   if (dt == J2D_F64) {
     const dim3 grd = adj ? persistent_grid(onestep_kernel<double, true, kOneRows>, g, 2, kOneRows)
                          : persistent_grid(onestep_kernel<double, false, kOneRows>, g, 2, kOneRows);
@@ -530,6 +634,46 @@ cudaError_t measure_exact(double *rate) {
   cudaFree(buf);
   if (e != cudaSuccess) return e;
   *rate = (double)grid * blk * iters * 4 / (best * 1e-3);
+  return cudaSuccess;
+}
+
+cudaError_t measure_exact_box(double *rate) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int blk = 256, grid = sms * 8, iters = 200;
+  void *buf = nullptr;
+  if ((e = cudaMalloc(&buf, sizeof(double) * grid * blk)) != cudaSuccess) return e;
+  const double w[9] = {0.11, 0.12, 0.1, 0.115, 0.105, 0.11, 0.1, 0.12, 0.11};  // positive, summing to 1
+  const Box9<double> b = box_chain<double>(w);
+  ExactWN<9> u;
+  u.ok = true;
+  for (int i = 0; i < 9; ++i) {
+    uint64_t bits;
+    memcpy(&bits, &b.w[i], 8);
+    u.e[i] = (int)(bits >> 52);
+    u.m[i] = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    exact_rate_box_kernel<<<grid, blk>>>((double *)buf, iters, u, b);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return e;
+  *rate = (double)grid * blk * iters * 2 / (best * 1e-3);
   return cudaSuccess;
 }
 

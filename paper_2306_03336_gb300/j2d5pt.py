@@ -48,6 +48,8 @@ def load():
     sig = {
         "j2d5pt_plan": [PP, I, I, I, P],
         "j2d5pt_plan_batched": [PP, I, P, P, I, P],
+        "j2d9pt_plan": [PP, I, I, I, P],
+        "j2d9pt_measure_exact_rate": [ctypes.POINTER(D)],
         "j2d5pt_plan_destroy": [P],
         "j2d5pt_layout": [P, I, ctypes.POINTER(L), ctypes.POINTER(L)],
         "j2d5pt_set_weights": [P, I, P],
@@ -119,6 +121,22 @@ def j2d5pt_plan(nx, ny, dtype, weights):
     w = np.ascontiguousarray(weights, dtype=np.float64)
     _check(load().j2d5pt_plan(ctypes.byref(h), int(nx), int(ny), int(dtype), w.ctypes.data_as(ctypes.c_void_p)))
     return h
+
+
+def j2d9pt_plan(nx, ny, dtype, weights):
+    """Plan for the 3x3 box stencil: nine weights, rows y-1, y, y+1, columns x-1, x, x+1."""
+    h = ctypes.c_void_p()
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+    if w.size != 9:
+        raise ValueError("the box stencil takes nine weights")
+    _check(load().j2d9pt_plan(ctypes.byref(h), int(nx), int(ny), int(dtype), w.ctypes.data_as(ctypes.c_void_p)))
+    return h
+
+
+def j2d9pt_measure_exact_rate():
+    r = ctypes.c_double()
+    _check(load().j2d9pt_measure_exact_rate(ctypes.byref(r)))
+    return r.value
 
 
 def j2d5pt_plan_batched(nx, ny, dtype, weights):
@@ -253,7 +271,12 @@ class Plan:
     def __init__(self, nx, ny=None, dtype="f64", weights=None, batched=False):
         self.dtype = dtype
         self.code = _DT[dtype]
-        if batched:
+        self.box = not batched and np.asarray(weights).size == 9
+        if self.box:
+            self.sizes = [(int(nx), int(ny))]
+            self.weights = np.asarray(weights, dtype=np.float64).reshape(1, 9)
+            self.handle = j2d9pt_plan(nx, ny, self.code, self.weights[0])
+        elif batched:
             sizes = list(nx)
             self.sizes = [(int(a), int(b)) for a, b in sizes]
             w = np.asarray(weights, dtype=np.float64).reshape(len(sizes), 5)
@@ -269,6 +292,14 @@ class Plan:
     @classmethod
     def batch(cls, sizes, dtype, weights):
         return cls(sizes, None, dtype, weights, batched=True)
+
+    @classmethod
+    def box9(cls, nx, ny, dtype, weights):
+        """A 3x3 box (j2d9pt) plan; weights row by row from the y-1 row, x-1 first."""
+        w = np.asarray(weights, dtype=np.float64).reshape(-1)
+        if w.size != 9:
+            raise ValueError("the box stencil takes nine weights")
+        return cls(nx, ny, dtype, w)
 
     def close(self):
         if self.handle is not None:

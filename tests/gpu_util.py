@@ -38,10 +38,11 @@ def f32_bound(steps):
     return (1 + 12 * max(steps, 1)) * 2.0 ** -24
 
 
-def window_block(oracle, u0, w, steps, y0, y1, x0, x1, threads=None):
+def window_block(oracle, u0, w, steps, y0, y1, x0, x1, threads=None, box=False):
     """Oracle values of the cells [y0, y1) x [x0, x1) of u0 (array coordinates,
     ring included) after `steps` steps.  A cell's value after T steps depends
-    only on the initial cells within distance T, so the oracle runs on the
+    only on the initial cells within distance T (also for the 3x3 box,
+    box=True), so the oracle runs on the
     block plus a margin of T+1 cells (clipped at the array; the margin's edge is
     held constant, and its changes cannot reach the block within T steps)."""
     H, W = u0.shape
@@ -51,7 +52,7 @@ def window_block(oracle, u0, w, steps, y0, y1, x0, x1, threads=None):
     win = np.ascontiguousarray(u0[a0:a1, b0:b1])
     if threads is None:
         threads = oracle.max_threads()
-    out = oracle.run(win, w, steps, threads=threads)
+    out = (oracle.box_run if box else oracle.run)(win, w, steps, threads=threads)
     return out[y0 - a0:y1 - a0, x0 - b0:x1 - b0]
 
 

@@ -24,7 +24,7 @@ def lib():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(j2d5pt_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(j2d[59]pt_[a-z_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
