@@ -6,7 +6,8 @@ steps per benchmark step (one benchmark step = one j2d5pt_run of 1000 time
 steps).  The plan is autotuned first (one-step / resident / bands / tiles over
 temporal depths and tile shapes), then timed.  The other workloads (FP64
 2048 x 1536, FP32 16384^2, the paper's 8592 x 8328 domain, 256 batched grids,
-the 4096^2 gradient) are reported under "extras", each with the one-step
+the 4096^2 gradient, the 3x3 box stencil j2d9pt at 16384^2) are reported
+under "extras", each with the one-step
 kernel beside it and its own roofline record (median of 3 repetitions).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -497,7 +498,46 @@ def run_extras(j2d5pt, synth, flush, stream, pk, head_plan, head_src, head_dst):
     del srcs, dsts
     torch.cuda.empty_cache()
 
-    # 6) gradient of L = <g, u_T>, 4096^2 FP64, 500 steps, checkpoints every 50
+    # 6) the second stencil shape, the 3x3 box (j2d9pt): FP64 and FP32 16384^2,
+    #    1000 steps, autotuned, beside its one-step kernel; FP64 against the
+    #    arithmetic peak of the nine-term cell (FP64 pipe: 9 FMA instructions
+    #    per chain cell; integer path: the measured nine-term rate; 17 flops per cell)
+    n, T = HEAD_N, HEAD_T
+    cells = n * n * T
+    u0 = synth.field(n, n, synth.data_seed(1))
+    wb = synth.box_weights(synth.weight_seed(1))
+    exact9 = j2d5pt.j2d9pt_measure_exact_rate()
+    f = pk["share"]
+    alu9 = 1.0 / max((1.0 - f) / (pk["fma64"] / 9), f / exact9 if f else 0.0)
+    box = {"exact9_gcells": round(exact9 / 1e9, 2), "peak_gcells": round(alu9 / 1e9, 2)}
+    for dt in ("f64", "f32"):
+        p = j2d5pt.Plan.box9(n, n, dt, wb)
+        a, b = p.to_device(u0 if dt == "f64" else u0.astype(np.float32)), p.empty()
+        p.set("algo", "onestep").set("timing", 1)
+        r1 = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
+        p.set("algo", "auto")
+        p.autotune(a, b, T)
+        p.set("timing", 1)
+        r2 = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
+        r2["plan"] = p.describe()
+        if dt == "f64":
+            for r in (r1, r2):
+                g = r["kernel_gcells"]
+                r["roofline"] = {"bound": "alu", "achieved": round(g * 17 / 1e3, 4),
+                                 "peak": round(alu9 / 1e9 * 17 / 1e3, 4), "unit": "TFLOP/s",
+                                 "frac": round(g * 1e9 / alu9, 4),
+                                 "peak_source": "of measured: FP64 pipe / 9 per chain cell, nine-term integer path "
+                                                "(j2d9pt_measure_exact_rate), exact share %.3f; x 17 flops" % f}
+        else:
+            r1["roofline"] = roof_hbm(pk, r1["kernel_gcells"], 4)
+            r2["roofline"] = roof_f32_dtb(pk, r2["kernel_gcells"], 1)
+        box[dt] = {"onestep": r1, "autotuned": r2}
+        p.close()
+        del a, b
+        torch.cuda.empty_cache()
+    out["box9_16384x16384_1000"] = box
+
+    # 7) gradient of L = <g, u_T>, 4096^2 FP64, 500 steps, checkpoints every 50
     from paper_2306_03336_gb300.autograd import J2D5PT
     cfg = synth.WORKLOADS["j2d5pt_f64_4096x4096_500_adjoint"]
     n, T = cfg["nx"], cfg["steps"]

@@ -27,6 +27,13 @@ def weights(seed):
     return w / w.sum()
 
 
+def box_weights(seed):
+    """Nine uniform [0,1) values divided by their FP64 sum: the 3x3 box
+    weights, rows y-1, y, y+1, columns x-1, x, x+1."""
+    w = rng(seed).random(9)
+    return w / w.sum()
+
+
 def dyadic_weights():
     """Weights that are exact binary fractions summing exactly to 1."""
     return np.array([1 / 8, 1 / 8, 1 / 4, 1 / 4, 1 / 4])

@@ -22,9 +22,7 @@ def _built():
     __graft_entry__.build()
 
 
-def box_weights(seed):
-    w = synth.rng(seed).random(9)
-    return w / w.sum()
+box_weights = synth.box_weights
 
 
 W_DYADIC = np.array([1, 1, 2, 2, 3, 2, 1, 3, 1], dtype=np.float64) / 16

@@ -39,9 +39,7 @@ def _read_golden():
     return nx, ny, y0, x0, w, cells
 
 
-def _box_weights(seed):
-    w = synth.rng(seed).random(9)
-    return w / w.sum()
+_box_weights = synth.box_weights
 
 
 def test_box_impulse_golden(oracle_mod):
