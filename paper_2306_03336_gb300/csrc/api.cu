@@ -117,7 +117,9 @@ static j2d_status plan_common(j2d5pt_plan_t *out, int count, const int *nx, cons
   cudaDeviceProp prop;
   if ((e = cudaGetDeviceProperties(&prop, p->device)) != cudaSuccess) { delete p; return cuda_fail(e, "plan: properties"); }
   p->sms = prop.multiProcessorCount;
-  p->smem_optin = prop.sharedMemPerBlockOptin;
+  // the checked build keeps static shared memory per block (its bound-test
+  // range, padded to the 1024-byte alignment of the dynamic shared memory)
+  p->smem_optin = prop.sharedMemPerBlockOptin - (kChecked ? 1024 : 0);
   size_t ws_bytes = 0;
   long max_partials = 0;
   for (int i = 0; i < count; ++i) {
@@ -542,6 +544,7 @@ extern "C" j2d_status j2d5pt_sync_status(j2d5pt_plan_t p) {
   int st = 0;
   if ((e = cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "sync_status: read");
+  if (st == 0) st = dtb_bounds_fault();
   if (st != 0) {
     cudaMemset(p->d_status, 0, sizeof(int));
     if (st == J2D_ERR_TIMEOUT) return fail(J2D_ERR_TIMEOUT, "device: a wait exceeded the time limit; results invalid");
@@ -739,4 +742,6 @@ extern "C" long j2d5pt_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" const char *j2d5pt_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" const char *j2d5pt_version(void) { return "j2d5pt-gb300 0.1 (sm_103a)"; }
+extern "C" const char *j2d5pt_version(void) {
+  return kChecked ? "j2d5pt-gb300 0.2 (sm_103a, bounds-checked build)" : "j2d5pt-gb300 0.2 (sm_103a)";
+}

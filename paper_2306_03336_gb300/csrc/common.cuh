@@ -375,6 +375,28 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
+// ---- the checked build (-DJ2D_BOUNDS_CHECK) --------------------------------------
+// The blocked kernels reach shared and global memory through ldm / stm / vload /
+// vstore (dtb.cu).  In the checked build every such access is tested first: a
+// shared address against the launch's dynamic shared memory, a global address
+// against the range of the buffers the launch may touch (set at kernel start);
+// a failed test records J2D_ERR_BOUNDS (reported by j2d5pt_sync_status) and the
+// access is skipped (a load reads zero).  The regular build compiles the tests
+// away: kChecked is false and the accessors are plain loads and stores.
+#ifdef J2D_BOUNDS_CHECK
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+__device__ __forceinline__ bool smem_window_ok(const void *p, unsigned bytes) {
+  extern __shared__ char j2d_dynamic_smem[];
+  unsigned size;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+  const uint32_t a = smem_u32(p), b = smem_u32(j2d_dynamic_smem);
+  return a >= b && a + bytes <= b + size;
+}
+
 // Record the first device-side error of a run; later errors are dropped.
 __device__ __forceinline__ void set_error(int *status, int code) {
   if (status) atomicCAS(status, DEV_OK, code);

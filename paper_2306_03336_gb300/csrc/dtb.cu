@@ -101,6 +101,7 @@ struct KParams {
   unsigned long long timeout_ns;
   int mute_slot;            // fault injection: this slot never publishes its step counter (-1: none)
   int int_path;             // FP64: the kExactMask cells on the integer path
+  unsigned long long mem_lo, mem_hi;  // checked build: the global range this launch may touch
   void *skewbuf;            // SKEWED: per CTA [2 parities][levels][2 rows][skew_tw] elements
   int skew_tw, skew_levels, skew_wx;  // SKEWED: band width (elements), levels per parity, strips across
 };
@@ -146,6 +147,44 @@ __host__ __device__ inline size_t pair_smem_bytes(int elem, int rmax) {
   return (size_t)kHeaderBytes + (size_t)kWarps * pair_region_elems(elem, rmax) * elem;
 }
 
+// ---- memory accessors (tested in the checked build) --------------------------
+
+#ifdef J2D_BOUNDS_CHECK
+__device__ int g_bounds_fault;                       // J2D_ERR_BOUNDS once a test failed
+__shared__ unsigned long long s_mem_lo, s_mem_hi;    // global range the launch may touch
+#endif
+
+// Is [p, p + bytes) inside the launch's shared memory (shared addresses) or
+// inside the launch's global range?  Always true in the regular build.
+__device__ __forceinline__ bool access_ok(const void *p, unsigned bytes) {
+#ifdef J2D_BOUNDS_CHECK
+  bool ok;
+  if (__isShared(p)) {
+    ok = smem_window_ok(p, bytes);
+  } else {
+    const unsigned long long a = (unsigned long long)p;
+    ok = a >= s_mem_lo && a + bytes <= s_mem_hi;
+  }
+  if (!ok) atomicCAS(&g_bounds_fault, DEV_OK, DEV_BOUNDS);
+  return ok;
+#else
+  (void)p;
+  (void)bytes;
+  return true;
+#endif
+}
+template <typename T> __device__ __forceinline__ T ldm(const T *p) {
+  if (kChecked && !access_ok(p, sizeof(T))) return T(0);
+  return *p;
+}
+template <typename T> __device__ __forceinline__ void stm(T *p, T v) {
+  if (!kChecked || access_ok(p, sizeof(T))) *p = v;
+}
+template <typename T> __device__ __forceinline__ T ld_cg_chk(const T *p) {
+  if (kChecked && !access_ok(p, sizeof(T))) return T(0);
+  return ld_cg(p);
+}
+
 // ---- bounded waits ---------------------------------------------------------
 
 __device__ __forceinline__ bool expired(uint64_t deadline, int *status) {
@@ -159,6 +198,7 @@ __device__ __forceinline__ bool expired(uint64_t deadline, int *status) {
 
 // All lanes wait until *flag >= target (acquire); false on timeout / error.
 __device__ __forceinline__ bool wait_flag(const int *flag, bool global, int target, const KParams &kp) {
+  if (kChecked && !access_ok(flag, 4)) return false;
   const uint64_t deadline = globaltimer_ns() + kp.timeout_ns;
   for (int it = 0;; ++it) {
     const int v = global ? ld_acquire_gpu(flag) : ld_acquire_cta(flag);
@@ -215,6 +255,10 @@ struct Strip {
 
 template <typename T>
 __device__ __forceinline__ void vload(const T *p, bool global, T *o) {
+  if (kChecked && !access_ok(p, 16)) {
+    for (int e = 0; e < 16 / (int)sizeof(T); ++e) o[e] = T(0);
+    return;
+  }
   if constexpr (sizeof(T) == 8) {
     double2 v = global ? __ldcg(reinterpret_cast<const double2 *>(p)) : *reinterpret_cast<const double2 *>(p);
     o[0] = v.x; o[1] = v.y;
@@ -225,6 +269,7 @@ __device__ __forceinline__ void vload(const T *p, bool global, T *o) {
 }
 template <typename T>
 __device__ __forceinline__ void vstore(T *p, const T *o) {
+  if (kChecked && !access_ok(p, 16)) return;
   if constexpr (sizeof(T) == 8) {
     *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
   } else {
@@ -250,7 +295,7 @@ __device__ __forceinline__ void sweep_row(T (&ra)[VecOf<T>::V], T (&rb)[VecOf<T>
                                           RingAcc<T> &rg) {
   constexpr int V = VecOf<T>::V;
   constexpr int SW = 32 * V;
-  const T h = hcol[r];
+  const T h = ldm(&hcol[r]);
   T left = __shfl_up_sync(0xffffffffu, rb[V - 1], 1);
   T right = __shfl_down_sync(0xffffffffu, rb[0], 1);
   if (lane == 0) left = h;
@@ -339,13 +384,13 @@ __device__ __forceinline__ void ring_accumulate(RingAcc<T> &rg, const T *data, c
     for (int e = 0; e < V; ++e) rg.yp[e] = add_rn(rg.yp[e], mul_rn(rg.N, v[e]));
   }
   if (rg.ring & (1 << SIDE_XM)) {
-    if (lane < rows) rg.xm0 = fma_rn(rg.W, data[lane * SW], rg.xm0);
-    if (lane + 32 < rows) rg.xm1 = fma_rn(rg.W, data[(lane + 32) * SW], rg.xm1);
+    if (lane < rows) rg.xm0 = fma_rn(rg.W, ldm(&data[lane * SW]), rg.xm0);
+    if (lane + 32 < rows) rg.xm1 = fma_rn(rg.W, ldm(&data[(lane + 32) * SW]), rg.xm1);
   }
   if (rg.ring & (1 << SIDE_XP)) {
     const int c = rg.xp_lane * V + rg.xp_elem;  // strip column of grid column nx
-    if (lane < rows) rg.xp0 = fma_rn(rg.E, data[lane * SW + c], rg.xp0);
-    if (lane + 32 < rows) rg.xp1 = fma_rn(rg.E, data[(lane + 32) * SW + c], rg.xp1);
+    if (lane < rows) rg.xp0 = fma_rn(rg.E, ldm(&data[lane * SW + c]), rg.xp0);
+    if (lane + 32 < rows) rg.xp1 = fma_rn(rg.E, ldm(&data[(lane + 32) * SW + c]), rg.xp1);
   }
 }
 
@@ -366,7 +411,8 @@ __device__ void strip_store(const Strip &st, const GridDev &gd, const T *data, c
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) {
-      for (int r = st.sy0; r < st.sy1; ++r) tma_store_2d(map_store, off + st.x0, st.y0 + r, data + r * SW);
+      for (int r = st.sy0; r < st.sy1; ++r)
+        if (!kChecked || access_ok(data + r * SW, SW * sizeof(T))) tma_store_2d(map_store, off + st.x0, st.y0 + r, data + r * SW);
       bulk_commit();
       // a tensor store may rewrite the rest of the 16-byte granule holding
       // column nx, i.e. the ring cell nx+1: let it land before the adjoint
@@ -383,7 +429,7 @@ __device__ void strip_store(const Strip &st, const GridDev &gd, const T *data, c
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         const int c = lane * V + e;
-        if (c >= st.sx0 && c < st.sx1) dstbuf[rowoff + st.x0 + c] = data[r * SW + c];
+        if (c >= st.sx0 && c < st.sx1) stm(&dstbuf[rowoff + st.x0 + c], ldm(&data[r * SW + c]));
       }
     }
   }
@@ -393,19 +439,19 @@ __device__ void strip_store(const Strip &st, const GridDev &gd, const T *data, c
     for (int e = 0; e < V; ++e) {
       const int c = lane * V + e, x = st.x0 + c;
       const bool xin = x >= 1 && x <= nx && c >= st.sx0 && c < st.sx1;
-      if ((st.ring & (1 << SIDE_YM)) && xin && st.sy0 == 0) dstbuf[off + x] = rg.ym[e];
-      if ((st.ring & (1 << SIDE_YP)) && xin && st.sy1 == rows) dstbuf[(long)(ny + 1) * pitch + off + x] = rg.yp[e];
+      if ((st.ring & (1 << SIDE_YM)) && xin && st.sy0 == 0) stm(&dstbuf[off + x], rg.ym[e]);
+      if ((st.ring & (1 << SIDE_YP)) && xin && st.sy1 == rows) stm(&dstbuf[(long)(ny + 1) * pitch + off + x], rg.yp[e]);
     }
     if ((st.ring & (1 << SIDE_XM)) && st.sx0 == 0) {
-      if (lane < rows && lane >= st.sy0 && lane < st.sy1) dstbuf[(long)(st.y0 + lane) * pitch + off] = rg.xm0;
+      if (lane < rows && lane >= st.sy0 && lane < st.sy1) stm(&dstbuf[(long)(st.y0 + lane) * pitch + off], rg.xm0);
       if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
-        dstbuf[(long)(st.y0 + lane + 32) * pitch + off] = rg.xm1;
+        stm(&dstbuf[(long)(st.y0 + lane + 32) * pitch + off], rg.xm1);
     }
     if ((st.ring & (1 << SIDE_XP)) && (nx - st.x0) < st.sx1) {
       if (lane < rows && lane >= st.sy0 && lane < st.sy1)
-        dstbuf[(long)(st.y0 + lane) * pitch + off + nx + 1] = rg.xp0;
+        stm(&dstbuf[(long)(st.y0 + lane) * pitch + off + nx + 1], rg.xp0);
       if (lane + 32 < rows && lane + 32 >= st.sy0 && lane + 32 < st.sy1)
-        dstbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1] = rg.xp1;
+        stm(&dstbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1], rg.xp1);
     }
   }
 }
@@ -480,7 +526,7 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
     if constexpr (kLocalFlags) {
       fence_acq_rel_cta();
       __syncwarp();
-      if (lane == 0) st_relaxed_cta(sflags + warp, value);
+      if (lane == 0 && (!kChecked || access_ok(sflags + warp, 4))) st_relaxed_cta(sflags + warp, value);
       __syncwarp();
     }
   };
@@ -488,7 +534,8 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
     if (!any_remote) return;
     fence_acq_rel_gpu();
     __syncwarp();
-    if (lane == 0 && slot != kp.mute_slot) st_relaxed_gpu(kp.gflags + slot, value);
+    if (lane == 0 && slot != kp.mute_slot && (!kChecked || access_ok(kp.gflags + slot, 4)))
+      st_relaxed_gpu(kp.gflags + slot, value);
     __syncwarp();
   };
 
@@ -522,9 +569,9 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
       vstore(outbox[SIDE_YP] + par * SW + lane * V, o);
     }
     if (outbox[SIDE_XM])
-      for (int r = lane; r < rows; r += 32) outbox[SIDE_XM][par * rp + r] = data[r * SW];
+      for (int r = lane; r < rows; r += 32) stm(&outbox[SIDE_XM][par * rp + r], ldm(&data[r * SW]));
     if (outbox[SIDE_XP])
-      for (int r = lane; r < rows; r += 32) outbox[SIDE_XP][par * rp + r] = data[r * SW + SW - 1];
+      for (int r = lane; r < rows; r += 32) stm(&outbox[SIDE_XP][par * rp + r], ldm(&data[r * SW + SW - 1]));
   };
 
   if (act) {
@@ -533,8 +580,10 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
     __syncwarp();
     if (lane == 0) {
       bulk_wait_read_all();  // previous strip's stores have read shared memory
-      mbar_expect_tx(&bars[warp], (uint32_t)(SW * kp.rmax * sizeof(T)));
-      tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
+      const uint32_t bytes = (uint32_t)(SW * kp.rmax * sizeof(T));
+      const bool ok = !kChecked || access_ok(data, bytes);  // a refused load still completes the phase
+      mbar_expect_tx(&bars[warp], ok ? bytes : 0u);
+      if (ok) tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
     }
     // constant halos (ring in the forward map, overlapped-halo edge rows/columns)
 #pragma unroll
@@ -550,7 +599,7 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
 #pragma unroll
         for (int e = 0; e < V; ++e) {
           const int x = xl + e;
-          v[e] = (!zero && x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+          v[e] = (!zero && x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? ldm(&srcbuf[(long)y * pitch + off + x]) : T(0);
         }
         vstore(box + lane * V, v);
         vstore(box + len + lane * V, v);
@@ -558,9 +607,9 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
         const int x = s == SIDE_XM ? st.x0 - 1 : st.x0 + SW;
         for (int r = lane; r < rows; r += 32) {
           const int y = st.y0 + r;
-          const T v = (!zero && x >= 0 && x <= nx + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
-          box[r] = v;
-          box[len + r] = v;
+          const T v = (!zero && x >= 0 && x <= nx + 1) ? ldm(&srcbuf[(long)y * pitch + off + x]) : T(0);
+          stm(&box[r], v);
+          stm(&box[len + r], v);
         }
       }
     }
@@ -570,16 +619,16 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
       for (int e = 0; e < V; ++e) {
         const int x = xl + e;
         const bool xin = x >= 1 && x <= nx;
-        if ((st.ring & (1 << SIDE_YM)) && xin) rg.ym[e] = srcbuf[off + x];
-        if ((st.ring & (1 << SIDE_YP)) && xin) rg.yp[e] = srcbuf[(long)(ny + 1) * pitch + off + x];
+        if ((st.ring & (1 << SIDE_YM)) && xin) rg.ym[e] = ldm(&srcbuf[off + x]);
+        if ((st.ring & (1 << SIDE_YP)) && xin) rg.yp[e] = ldm(&srcbuf[(long)(ny + 1) * pitch + off + x]);
       }
       if (st.ring & (1 << SIDE_XM)) {
-        if (lane < rows) rg.xm0 = srcbuf[(long)(st.y0 + lane) * pitch + off];
-        if (lane + 32 < rows) rg.xm1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off];
+        if (lane < rows) rg.xm0 = ldm(&srcbuf[(long)(st.y0 + lane) * pitch + off]);
+        if (lane + 32 < rows) rg.xm1 = ldm(&srcbuf[(long)(st.y0 + lane + 32) * pitch + off]);
       }
       if (st.ring & (1 << SIDE_XP)) {
-        if (lane < rows) rg.xp0 = srcbuf[(long)(st.y0 + lane) * pitch + off + nx + 1];
-        if (lane + 32 < rows) rg.xp1 = srcbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1];
+        if (lane < rows) rg.xp0 = ldm(&srcbuf[(long)(st.y0 + lane) * pitch + off + nx + 1]);
+        if (lane + 32 < rows) rg.xp1 = ldm(&srcbuf[(long)(st.y0 + lane + 32) * pitch + off + nx + 1]);
       }
     }
     wait_mbar(&bars[warp], mbar_phase, kp);
@@ -589,7 +638,7 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
 #pragma unroll
       for (int e = 0; e < V; ++e)
         if (xl + e == nx + 1)
-          for (int r = 0; r < rows; ++r) drow[r * SW + e] = T(0);
+          for (int r = 0; r < rows; ++r) stm(&drow[r * SW + e], T(0));
     }
     __syncwarp();
     // ---- publish state-0 edges into the neighbours' parity-0 mailboxes ----
@@ -623,7 +672,7 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
         if (!remote[s]) continue;
         T *sb = mbox + L::side_off(s, rp) + par * rp;
         const T *gb = inbox[s] + par * rp;
-        for (int r = lane; r < rows; r += 32) sb[r] = ld_cg(gb + r);
+        for (int r = lane; r < rows; r += 32) stm(&sb[r], ld_cg_chk(gb + r));
       }
       __syncwarp();
       const T *hcol = mbox + L::side_off(hside, rp) + par * rp;
@@ -713,7 +762,7 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
 #pragma unroll
     for (int e = 0; e < V; ++e) c0[e] = p0[e];
   }
-  row_update<T, DEAD>(a0, b0, c0, hct[0], hct[0], lane, a, u, ip, xl, y0, dead, b1);  // step t+1 of row 0
+  row_update<T, DEAD>(a0, b0, c0, ldm(&hct[0]), ldm(&hct[0]), lane, a, u, ip, xl, y0, dead, b1);  // step t+1 of row 0
 #pragma unroll
   for (int e = 0; e < V; ++e) {
     a0[e] = b0[e];
@@ -727,8 +776,8 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
 #pragma unroll kUnroll
   for (int r = 1; r < rows - 1; ++r) {
     vload(drow + (r + 1) * SW, false, c0);
-    row_update<T, DEAD>(a0, b0, c0, hct[r], hct[r], lane, a, u, ip, xl, y0 + r, dead, n1);  // step t+1 of row r
-    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, u, ip, xl, y0 + r - 1, dead, o);  // t+2, row r-1
+    row_update<T, DEAD>(a0, b0, c0, ldm(&hct[r]), ldm(&hct[r]), lane, a, u, ip, xl, y0 + r, dead, n1);  // step t+1 of row r
+    row_update<T, DEAD>(a1, b1, n1, ldm(&hct1[r - 1]), ldm(&hct1[r - 1]), lane, a, u, ip, xl, y0 + r - 1, dead, o);  // t+2, row r-1
     vstore(drow + (r - 1) * SW, o);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -740,8 +789,8 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
   }
   if (rows > 1) {
     const int r = rows - 1;
-    row_update<T, DEAD>(a0, b0, p0, hct[r], hct[r], lane, a, u, ip, xl, y0 + r, dead, n1);  // step t+1 of the last row
-    row_update<T, DEAD>(a1, b1, n1, hct1[r - 1], hct1[r - 1], lane, a, u, ip, xl, y0 + r - 1, dead, o);  // t+2, row R-2
+    row_update<T, DEAD>(a0, b0, p0, ldm(&hct[r]), ldm(&hct[r]), lane, a, u, ip, xl, y0 + r, dead, n1);  // step t+1 of the last row
+    row_update<T, DEAD>(a1, b1, n1, ldm(&hct1[r - 1]), ldm(&hct1[r - 1]), lane, a, u, ip, xl, y0 + r - 1, dead, o);  // t+2, row R-2
     vstore(drow + (r - 1) * SW, o);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -749,7 +798,7 @@ __device__ __forceinline__ void sweep_pair(T *drow, const T *hct, const T *hct1,
       b1[e] = n1[e];
     }
   }
-  row_update<T, DEAD>(a1, b1, p0n, hct1[rows - 1], hct1[rows - 1], lane, a, u, ip, xl, y0 + rows - 1, dead, o);  // t+2, last row
+  row_update<T, DEAD>(a1, b1, p0n, ldm(&hct1[rows - 1]), ldm(&hct1[rows - 1]), lane, a, u, ip, xl, y0 + rows - 1, dead, o);  // t+2, last row
   vstore(drow + (rows - 1) * SW, o);
 }
 
@@ -812,15 +861,17 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
   T xm2 = T(0), xm1 = T(0), xp0 = T(0), xp1 = T(0);  // columns -2, -1, SW, SW+1 of row `lane`
   T ctl = T(0), ctr = T(0), cbl = T(0), cbr = T(0);  // the diagonal cells
   auto gval = [&](int y, int x) -> T {
-    return (x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+    return (x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? ldm(&srcbuf[(long)y * pitch + off + x]) : T(0);
   };
   if (act) {
     fence_proxy_async_all();  // earlier generic writes before the async-proxy load
     __syncwarp();
     if (lane == 0) {
       bulk_wait_read_all();  // previous strip's stores have read shared memory
-      mbar_expect_tx(&bars[warp], (uint32_t)(SW * kp.rmax * sizeof(T)));
-      tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
+      const uint32_t bytes = (uint32_t)(SW * kp.rmax * sizeof(T));
+      const bool ok = !kChecked || access_ok(data, bytes);  // a refused load still completes the phase
+      mbar_expect_tx(&bars[warp], ok ? bytes : 0u);
+      if (ok) tma_load_2d(data, map_load, off + st.x0, st.y0, &bars[warp]);
     }
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -871,25 +922,25 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
       if (lane < rows) {
         if (wL >= 0) {
           const T *d = nbdata(wL) + lane * SW;
-          xm2 = d[SW - 2];
-          xm1 = d[SW - 1];
+          xm2 = ldm(&d[SW - 2]);
+          xm1 = ldm(&d[SW - 1]);
         }
         if (wR >= 0) {
           const T *d = nbdata(wR) + lane * SW;
-          xp0 = d[0];
-          xp1 = d[1];
+          xp0 = ldm(&d[0]);
+          xp1 = ldm(&d[1]);
         }
       }
-      if (wTL >= 0) ctl = nbdata(wTL)[(trows - 1) * SW + SW - 1];
-      if (wTR >= 0) ctr = nbdata(wTR)[(trows - 1) * SW];
-      if (wBL >= 0) cbl = nbdata(wBL)[SW - 1];
-      if (wBR >= 0) cbr = nbdata(wBR)[0];
+      if (wTL >= 0) ctl = ldm(&nbdata(wTL)[(trows - 1) * SW + SW - 1]);
+      if (wTR >= 0) ctr = ldm(&nbdata(wTR)[(trows - 1) * SW]);
+      if (wBL >= 0) cbl = ldm(&nbdata(wBL)[SW - 1]);
+      if (wBR >= 0) cbr = ldm(&nbdata(wBR)[0]);
       if (two) {
         // step t+1 on the ring around the strip
         T own0 = T(0), ownl = T(0);
         if (lane < rows) {
-          own0 = data[lane * SW];
-          ownl = data[lane * SW + SW - 1];
+          own0 = ldm(&data[lane * SW]);
+          ownl = ldm(&data[lane * SW + SW - 1]);
         }
         T up = __shfl_up_sync(0xffffffffu, xm1, 1), dn = __shfl_down_sync(0xffffffffu, xm1, 1);
         if (lane == 0) up = ctl;
@@ -901,8 +952,8 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
         if (lane == rows - 1) dn = cbr;
         const T r1 = wR >= 0 ? cell(st.x0 + SW, st.y0 + lane, ownl, xp1, up, xp0, dn) : xp0;
         if (lane < rows) {
-          hc[64 + lane] = l1;
-          hc[96 + lane] = r1;
+          stm(&hc[64 + lane], l1);
+          stm(&hc[96 + lane], r1);
         }
         T own[V];
         if (wT >= 0) {
@@ -921,8 +972,8 @@ __device__ void run_strip_pair(const Strip &st, const KParams &kp, char *smem, i
         }
       }
       if (lane < rows) {
-        hc[lane] = xm1;
-        hc[32 + lane] = xp0;
+        stm(&hc[lane], xm1);
+        stm(&hc[32 + lane], xp0);
       }
     }
     __syncthreads();  // every strip has read its neighbours' state-t cells
@@ -1015,7 +1066,7 @@ __device__ __forceinline__ void sweep_skew(T *drow, const T *hct, int rows, int 
 #pragma unroll kUnroll
   for (; r < r_hi; ++r) {
     vload(drow + r * SW, false, rc);
-    row_update<T, DEAD>(ra, rb, rc, hct[r], hct[r], lane, a, u, ip, xl, yb + r, dead, o);
+    row_update<T, DEAD>(ra, rb, rc, ldm(&hct[r]), ldm(&hct[r]), lane, a, u, ip, xl, yb + r, dead, o);
     vstore(drow + r * SW, o);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -1056,8 +1107,8 @@ __device__ __forceinline__ void sweep_skew_box(T *drow, const T *hct, int rows, 
     if (lane == 31) r = h;
   };
   T al, ar, bl, br, cl, cr;
-  sides(ra, hct[0], al, ar);
-  sides(rb, hct[1], bl, br);
+  sides(ra, ldm(&hct[0]), al, ar);
+  sides(rb, ldm(&hct[1]), bl, br);
   auto shift = [&]() {
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -1072,13 +1123,13 @@ __device__ __forceinline__ void sweep_skew_box(T *drow, const T *hct, int rows, 
   int r = 0;
   for (; r < r_lo; ++r) {
     vload(drow + r * SW, false, rc);
-    sides(rc, hct[r + 2], cl, cr);
+    sides(rc, ldm(&hct[r + 2]), cl, cr);
     vstore(drow + r * SW, rb);
     shift();
   }
   for (; r < r_hi; ++r) {
     vload(drow + r * SW, false, rc);
-    sides(rc, hct[r + 2], cl, cr);
+    sides(rc, ldm(&hct[r + 2]), cl, cr);
     const int y = yb + r;
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -1160,7 +1211,7 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
   auto sb = [&](int p, int lev, int row) { return sbuf + (((size_t)p * kp.skew_levels + lev) * 2 + row) * kp.skew_tw; };
   const bool bottom = act && rows >= 2 && y0 + rows == q0 + nq;
   auto gval = [&](int y, int x) -> T {
-    return (x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? srcbuf[(long)y * pitch + off + x] : T(0);
+    return (x >= 0 && x <= nx + 1 && y >= 0 && y <= ny + 1) ? ldm(&srcbuf[(long)y * pitch + off + x]) : T(0);
   };
 
   const int xl = x0 + lane * V;
@@ -1178,8 +1229,10 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
     __syncwarp();
     if (lane == 0) {
       bulk_wait_read_all();  // previous tile's stores have read shared memory
-      mbar_expect_tx(&bars[warp], (uint32_t)(SW * R * sizeof(T)));
-      tma_load_2d(data, map_load, off + x0, y0, &bars[warp]);
+      const uint32_t bytes = (uint32_t)(SW * R * sizeof(T));
+      const bool ok = !kChecked || access_ok(data, bytes);  // a refused load still completes the phase
+      mbar_expect_tx(&bars[warp], ok ? bytes : 0u);
+      if (ok) tma_load_2d(data, map_load, off + x0, y0, &bars[warp]);
     }
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -1231,15 +1284,15 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
         const int row = lane - H0;
         T hl, hr;
         if (wL >= 0)
-          hl = row >= 0 ? nbdata(wL)[row * SW + SW - 1] : wTL >= 0 ? nbdata(wTL)[(R + row) * SW + SW - 1] : pcl;
+          hl = row >= 0 ? ldm(&nbdata(wL)[row * SW + SW - 1]) : wTL >= 0 ? ldm(&nbdata(wTL)[(R + row) * SW + SW - 1]) : pcl;
         else
           hl = phl;  // the ring column, or zero at a band edge (overlapped halo)
         if (wR >= 0)
-          hr = row >= 0 ? nbdata(wR)[row * SW] : wTR >= 0 ? nbdata(wTR)[(R + row) * SW] : pcr;
+          hr = row >= 0 ? ldm(&nbdata(wR)[row * SW]) : wTR >= 0 ? ldm(&nbdata(wTR)[(R + row) * SW]) : pcr;
         else
           hr = phr;
-        hc[lane] = hl;
-        hc[32 + lane] = hr;
+        stm(&hc[lane], hl);
+        stm(&hc[32 + lane], hr);
       }
     }
     __syncthreads();  // every strip has read its neighbours' level-(L-1) cells
@@ -1250,8 +1303,8 @@ __device__ void run_strip_skew(const KParams &kp, const int *job, char *smem, in
           vload(sb(par ^ 1, L, 0) + (x0 - tx0) + lane * V, false, pa);
           vload(sb(par ^ 1, L, 1) + (x0 - tx0) + lane * V, false, pb);
           if (lane < H0) {
-            if (wL >= 0) pcl = sb(par ^ 1, L, 2 - H0 + lane)[x0 - 1 - tx0];
-            if (wR >= 0) pcr = sb(par ^ 1, L, 2 - H0 + lane)[x0 + SW - tx0];
+            if (wL >= 0) pcl = ldm(&sb(par ^ 1, L, 2 - H0 + lane)[x0 - 1 - tx0]);
+            if (wR >= 0) pcr = ldm(&sb(par ^ 1, L, 2 - H0 + lane)[x0 + SW - tx0]);
           }
         }
         if (x0 == 1) phl = gval(y0 + lane - L - H0, 0);
@@ -1413,7 +1466,18 @@ __device__ Strip group_strip(const KParams &kp, int j, int warp, int cta_slot0, 
 // Ring copy for every grid of a run in one launch: block (g, d) copies the
 // ring of grid g's input to its buffer d (1 = workspace, 2 = output).
 template <typename T>
-__global__ void ring_copy_grids_kernel(const GridDev *grids, int copy_ws, int copy_out) {
+__global__ void ring_copy_grids_kernel(const GridDev *grids, int copy_ws, int copy_out, unsigned long long mem_lo,
+                                       unsigned long long mem_hi) {
+#ifdef J2D_BOUNDS_CHECK
+  if (threadIdx.x == 0) {
+    s_mem_lo = mem_lo;
+    s_mem_hi = mem_hi;
+  }
+  __syncthreads();
+#else
+  (void)mem_lo;
+  (void)mem_hi;
+#endif
   const GridDev &g = grids[blockIdx.x];
   const int d = blockIdx.y == 0 ? 2 : 1;
   if ((d == 2 && !copy_out) || (d == 1 && !copy_ws) || g.buf[d] == g.buf[0]) return;
@@ -1431,7 +1495,7 @@ __global__ void ring_copy_grids_kernel(const GridDev *grids, int copy_ws, int co
       x = (j & 1) ? nx + 1 : 0;
     }
     const long e = (long)y * g.pitch + g.off + x;
-    out[e] = in[e];
+    stm(&out[e], ldm(&in[e]));
   }
 }
 
@@ -1446,6 +1510,12 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
     mbar_init(&bars[warp], 1);
     sflags[warp] = -1;
   }
+#ifdef J2D_BOUNDS_CHECK
+  if (threadIdx.x == 0) {
+    s_mem_lo = kp.mem_lo;
+    s_mem_hi = kp.mem_hi;
+  }
+#endif
   fence_mbar_init();
   fence_proxy_async_smem();
   __syncthreads();
@@ -2024,6 +2094,20 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
     return e;
   }
 
+  // the global range this launch may touch (grid buffers, scratch,
+  // descriptors): the checked build tests every global access against it
+  unsigned long long mem_lo = ~0ull, mem_hi = 0;
+  auto span = [&](const void *b, size_t n) {
+    mem_lo = std::min(mem_lo, (unsigned long long)b);
+    mem_hi = std::max(mem_hi, (unsigned long long)b + n);
+  };
+  for (size_t i = 0; i < ng; ++i)
+    for (int b = 0; b < 3; ++b) span(hg[i].buf[b], grids[i].bytes(elem));
+  span(S.scratch, scratch);
+  span(S.desc, desc_bytes);
+  kp.mem_lo = mem_lo;
+  kp.mem_hi = mem_hi;
+
   // ring of every buffer a round writes = ring of the input (constant forward;
   // corners and the starting values of the adjoint ring accumulation)
   int src0 = 0;
@@ -2031,9 +2115,9 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
     const GridDev *gd = reinterpret_cast<const GridDev *>(S.desc);
     note_launch();
     if (dt == J2D_F64)
-      ring_copy_grids_kernel<double><<<dim3((unsigned)ng, 2), 256, 0, s>>>(gd, rounds > 1, 1);
+      ring_copy_grids_kernel<double><<<dim3((unsigned)ng, 2), 256, 0, s>>>(gd, rounds > 1, 1, mem_lo, mem_hi);
     else
-      ring_copy_grids_kernel<float><<<dim3((unsigned)ng, 2), 256, 0, s>>>(gd, rounds > 1, 1);
+      ring_copy_grids_kernel<float><<<dim3((unsigned)ng, 2), 256, 0, s>>>(gd, rounds > 1, 1, mem_lo, mem_hi);
     if ((e = cudaGetLastError()) != cudaSuccess) { err = "ring copy"; return e; }
   }
   // overlapped halos read neighbours' cells: a round must not write its source
@@ -2102,6 +2186,20 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   }
   if (r.ev1) cudaEventRecord(r.ev1, s);
   return e;
+}
+
+int dtb_bounds_fault() {
+#ifdef J2D_BOUNDS_CHECK
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_fault, sizeof v) != cudaSuccess) return 0;
+  if (v) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_bounds_fault, &z, sizeof z);
+  }
+  return v;
+#else
+  return 0;
+#endif
 }
 
 void dtb_release(DtbState &S) {

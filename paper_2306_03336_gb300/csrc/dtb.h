@@ -63,6 +63,9 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
                      const DtbRequest &rq);
 cudaError_t dtb_run(DtbState &st, const DtbRun &r, cudaStream_t s, std::string &err);
 void dtb_release(DtbState &st);
+// Checked build: J2D_ERR_BOUNDS if a bound test failed since the last call
+// (and clears it); 0 otherwise, and always 0 in the regular build.
+int dtb_bounds_fault();
 void dtb_invalidate(DtbState &st);  // forget the uploaded descriptors (weights changed)
 
 }  // namespace j2d

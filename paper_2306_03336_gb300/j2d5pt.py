@@ -15,6 +15,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libj2d5pt.so")
+# the same library built with every memory access of the blocked kernels
+# tested against its buffer (J2D_BOUNDS_CHECK): for tests, not for speed
+LIB_CHECKED_PATH = os.path.join(_HERE, "libj2d5pt_checked.so")
 
 J2D_F64, J2D_F32 = 0, 1
 J2D_OK, J2D_ERR_ARG, J2D_ERR_ALIGN, J2D_ERR_NOMEM, J2D_ERR_DEVICE = 0, 1, 2, 3, 4
@@ -26,6 +29,7 @@ STATUS_NAMES = {0: "J2D_OK", 1: "J2D_ERR_ARG", 2: "J2D_ERR_ALIGN", 3: "J2D_ERR_N
                 5: "J2D_ERR_UNSUPPORTED", 6: "J2D_ERR_TIMEOUT", 7: "J2D_ERR_BOUNDS"}
 
 _lib = None
+_lib_checked = None
 
 
 class J2DError(RuntimeError):
@@ -37,12 +41,25 @@ class J2DError(RuntimeError):
 def load():
     """Load libj2d5pt.so (built by paper_2306_03336_gb300.build); raise if absent."""
     global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libj2d5pt.so is not built (run __graft_entry__.build()); "
-                           "the CUDA library is required, there is no fallback")
-    lib = ctypes.CDLL(LIB_PATH)
+    if _lib is None:
+        _lib = _open(LIB_PATH)
+    return _lib
+
+
+def load_checked():
+    """Load the bounds-checked build libj2d5pt_checked.so (a separate handle
+    with the same functions); raise if absent."""
+    global _lib_checked
+    if _lib_checked is None:
+        _lib_checked = _open(LIB_CHECKED_PATH)
+    return _lib_checked
+
+
+def _open(path):
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built (run __graft_entry__.build()); "
+                           "the CUDA library is required, there is no fallback" % os.path.basename(path))
+    lib = ctypes.CDLL(path)
     P, I, L, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
     PP = ctypes.POINTER(ctypes.c_void_p)
     sig = {
@@ -82,7 +99,6 @@ def load():
     lib.j2d5pt_kernel_launches.restype = ctypes.c_long
     lib.j2d5pt_version.argtypes = []
     lib.j2d5pt_version.restype = ctypes.c_char_p
-    _lib = lib
     return lib
 
 

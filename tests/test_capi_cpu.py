@@ -39,6 +39,16 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_checked_build_exports_every_declared_symbol(lib):
+    """The bounds-checked variant (J2D_BOUNDS_CHECK) is built beside the
+    regular library and exposes the same C ABI."""
+    chk = j2d5pt.load_checked()
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+    assert "bounds-checked" in chk.j2d5pt_version().decode()
+    assert "bounds-checked" not in j2d5pt.j2d5pt_version()
+
+
 def test_version_and_last_error(lib):
     assert "sm_103a" in j2d5pt.j2d5pt_version()
     assert isinstance(j2d5pt.j2d5pt_last_error(), str)
