@@ -619,7 +619,8 @@ def run_reference(args):
 
 
 # ---- named runs for profiling --------------------------------------------------
-# name: (nx, ny, dtype, algo, depth, tile_wx, steps, runs); algo "auto" = autotuned
+# name: (nx, ny, dtype, algo, depth, tile_wx, steps, runs); algo "auto" = autotuned,
+# "box:ALGO" = the 3x3 box stencil with that algorithm
 WORKLOADS = {
     "headline": (HEAD_N, HEAD_N, "f64", "auto", 0, 0, HEAD_T, 2),
     "f64tiles": (8192, 8192, "f64", "tiles", 4, 4, 8, 1),
@@ -629,6 +630,7 @@ WORKLOADS = {
     "f32tiles": (8192, 8192, "f32", "tiles", 16, 2, 16, 1),
     "f32skewed": (8192, 8192, "f32", "skewed", 16, 8, 32, 1),
     "f32onestep": (8192, 8192, "f32", "onestep", 0, 0, 4, 1),
+    "f64box": (8192, 8192, "f64", "box:skewed", 4, 4, 8, 1),
 }
 
 
@@ -642,7 +644,11 @@ def run_workload(name):
     nx, ny, dt, algo, depth, wx, steps, runs = WORKLOADS[name]
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    p = j2d5pt.Plan(nx, ny, dt, synth.weights(synth.weight_seed(1)))
+    if algo.startswith("box:"):
+        algo = algo[4:]
+        p = j2d5pt.Plan.box9(nx, ny, dt, synth.box_weights(synth.weight_seed(1)))
+    else:
+        p = j2d5pt.Plan(nx, ny, dt, synth.weights(synth.weight_seed(1)))
     u0 = synth.field(nx, ny, synth.data_seed(1))
     src = p.to_device(u0 if dt == "f64" else u0.astype(np.float32))
     dst = p.empty()
