@@ -63,7 +63,9 @@ typedef enum {
 typedef enum {
   J2D_ALGO_AUTO = 0,
   J2D_ALGO_ONESTEP = 1,  /* one launch per time step, streaming through HBM */
-  J2D_ALGO_RESIDENT = 2, /* whole grid held on chip for all steps; one persistent launch */
+  J2D_ALGO_RESIDENT = 2, /* whole grid held on chip for all steps; one persistent launch.  On a
+                            batch: the grids in waves, each wave's grids on chip together for all
+                            steps (every grid must fit on chip by itself) */
   J2D_ALGO_BANDS = 3,    /* GPU-wide bands of the grid, processed serially, k steps per visit */
   J2D_ALGO_TILES = 4,    /* independent per-CTA tiles with a k-deep overlapped halo */
   J2D_ALGO_SKEWED = 5    /* serial tiles in skewed order: each CTA advances a run of rows of a

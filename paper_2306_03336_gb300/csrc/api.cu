@@ -628,8 +628,8 @@ static j2d_status autotune_common(j2d5pt_plan_t p, const void *const *in, void *
     DtbRequest rq;
     rq.algo = J2D_ALGO_RESIDENT;
     rq.steps = steps;
-    if (single && dtb_choose(p->dtype, p->grids, p->sms, p->smem_optin, rq).algo == J2D_ALGO_RESIDENT)
-      cands.push_back({J2D_ALGO_RESIDENT, 0, 0});
+    if (dtb_choose(p->dtype, p->grids, p->sms, p->smem_optin, rq).algo == J2D_ALGO_RESIDENT)
+      cands.push_back({J2D_ALGO_RESIDENT, 0, 0});  // a batch: grouped resident (waves of grids on chip)
   }
   const int depths[] = {2, 4, 6, 8, 12, 16, 24, 32};
   const bool box = is_box(p);  // the box runs the one-step kernel or the skewed tiles

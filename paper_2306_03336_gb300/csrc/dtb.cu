@@ -35,6 +35,10 @@
 //             rows of a column band tile after tile, each tile taking its top
 //             halo at every step from the tile before it, so no halo is
 //             recomputed in y (run_strip_skew).
+// RESIDENT on a batch runs the grids in waves (MODE_GROUPS): the grids of a
+// wave are on chip together, each split into strips whose links stay inside
+// it, advanced all steps with the neighbour exchange, and stored; a grid
+// barrier separates the waves.
 // In RESIDENT and BANDS a CTA holds a block of strips (4 x 4 where the grid
 // allows; see choose_bx), so that most neighbours share its shared memory.
 // FP32 TILES strips take two steps per exchange (run_strip_pair), reading
@@ -60,7 +64,7 @@ constexpr int kWarps = 16;            // warps (strips) per CTA
 constexpr int kThreads = kWarps * 32;
 enum { SIDE_YM = 0, SIDE_YP = 1, SIDE_XM = 2, SIDE_XP = 3 };
 enum { LINK_CONST = -1, LINK_ZERO = -2 };
-enum { MODE_BANDS = 0, MODE_TILES = 1, MODE_TILES_PAIR = 2, MODE_SKEW = 3 };
+enum { MODE_BANDS = 0, MODE_TILES = 1, MODE_TILES_PAIR = 2, MODE_SKEW = 3, MODE_GROUPS = 4 };
 // A tile job: grid, tile origin (x, y), valid core [vx0, vx1) x [vy0, vy1),
 // first warp, strips across and down (only the strips inside the grid: a
 // CTA runs a group of partial tiles side by side), and in the first tile of
@@ -74,6 +78,10 @@ constexpr int kTileInts = 11;
 // piece (no predecessor in the CTA's list), and wxa, the strips across
 // inside the grid.
 constexpr int kSkewInts = 10;
+// A strip of a grouped-resident wave (RESIDENT for a batch), one record per
+// slot (CTA x 16 + warp) and wave: grid (-1: no strip), first cell (x0, y0),
+// rows, ring bits, and the four neighbour slots (SIDE_* order) or LINK_CONST.
+constexpr int kSlotInts = 9;
 
 // Per-grid data the kernel reads from global memory.
 struct GridDev {
@@ -104,6 +112,7 @@ struct KParams {
   unsigned long long mem_lo, mem_hi;  // checked build: the global range this launch may touch
   void *skewbuf;            // SKEWED: per CTA [2 parities][levels][2 rows][skew_tw] elements
   int skew_tw, skew_levels, skew_wx;  // SKEWED: band width (elements), levels per parity, strips across
+  int dead_all;             // RESIDENT / BANDS, FP64: some strip has dead columns, all take the dead-column sweep
 };
 
 // Layout of one warp's shared-memory region (elements of T).
@@ -303,16 +312,17 @@ __device__ __forceinline__ void sweep_row(T (&ra)[VecOf<T>::V], T (&rb)[VecOf<T>
   T o[V];
 #pragma unroll
   for (int e = 0; e < V; ++e) {
+    // a dead cell keeps its value and is not evaluated (its zero-filled
+    // neighbours would send it off the FP64 integer path onto the FMA chain)
+    if (DEAD && (dead & (1u << e))) {
+      o[e] = rb[e];
+      continue;
+    }
     const T xm = e == 0 ? left : rb[e - 1], xp = e == V - 1 ? right : rb[e + 1];
     if constexpr (std::is_same<T, double>::value)
       o[e] = stencil_cell(a, u, exact_cell(xl + e, y0 + r, ipath), xm, xp, ra[e], rb[e], rc[e]);
     else
       o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
-  }
-  if constexpr (DEAD) {
-#pragma unroll
-    for (int e = 0; e < V; ++e)
-      if (dead & (1u << e)) o[e] = rb[e];
   }
   vstore(drow + r * SW, o);
 #pragma unroll
@@ -651,7 +661,12 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
   // ---- k steps ----
   // lane 0 reads the x-1 halo column, lane 31 the x+1 one (other lanes: any)
   const int hside = lane == 31 ? SIDE_XP : SIDE_XM;
-  const bool any_dead = __any_sync(0xffffffffu, dead != 0);
+  // FP64 resident and bands: when any strip of the launch has dead columns
+  // every strip sweeps with the dead-column code, so that an SM's warps run
+  // one instantiation of the long integer-path loop (the two side by side
+  // measured 20% slower, and in these schedules every strip of a grid waits
+  // for the slowest; tiles measured no gain)
+  const bool any_dead = (sizeof(T) == 8 && kp.dead_all) || __any_sync(0xffffffffu, dead != 0);
   for (int t = 0; t < k; ++t) {
     if (act) {
       const int par = t & 1;
@@ -725,16 +740,15 @@ __device__ __forceinline__ void row_update(const T (&ra)[VecOf<T>::V], const T (
   if (lane == 31) right = hr;
 #pragma unroll
   for (int e = 0; e < V; ++e) {
+    if (DEAD && (dead & (1u << e))) {  // dead cells keep their value, unevaluated (as in sweep_row)
+      o[e] = rb[e];
+      continue;
+    }
     const T xm = e == 0 ? left : rb[e - 1], xp = e == V - 1 ? right : rb[e + 1];
     if constexpr (std::is_same<T, double>::value)
       o[e] = stencil_cell(a, u, exact_cell(xl + e, y, ipath), xm, xp, ra[e], rb[e], rc[e]);
     else
       o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
-  }
-  if constexpr (DEAD) {
-#pragma unroll
-    for (int e = 0; e < V; ++e)
-      if (dead & (1u << e)) o[e] = rb[e];
   }
 }
 
@@ -1133,11 +1147,14 @@ __device__ __forceinline__ void sweep_skew_box(T *drow, const T *hct, int rows, 
     const int y = yb + r;
 #pragma unroll
     for (int e = 0; e < V; ++e) {
+      if (DEAD && (dead & (1u << e))) {  // dead cells keep their value, unevaluated (as in sweep_row)
+        o[e] = rb[e];
+        continue;
+      }
       const T m0 = e == 0 ? al : ra[e - 1], m2 = e == V - 1 ? ar : ra[e + 1];
       const T c0 = e == 0 ? bl : rb[e - 1], c2 = e == V - 1 ? br : rb[e + 1];
       const T p0 = e == 0 ? cl : rc[e - 1], p2 = e == V - 1 ? cr : rc[e + 1];
       o[e] = stencil_box_cell(b, u, exact_cell(xl + e, y, ip), m0, ra[e], m2, c0, rb[e], c2, p0, rc[e], p2);
-      if (DEAD && (dead & (1u << e))) o[e] = rb[e];
     }
     vstore(drow + r * SW, o);
     shift();
@@ -1463,6 +1480,25 @@ __device__ Strip group_strip(const KParams &kp, int j, int warp, int cta_slot0, 
   return Strip{};
 }
 
+// This slot's strip in a grouped-resident wave (the record holds it whole).
+__device__ Strip slot_strip(const int *rec, int SWc) {
+  Strip st{};
+  st.active = rec[0] >= 0;
+  if (!st.active) return st;
+  st.g = rec[0];
+  st.x0 = rec[1];
+  st.y0 = rec[2];
+  st.rows = rec[3];
+  st.ring = rec[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) st.link[s] = rec[5 + s];
+  st.sy0 = 0;
+  st.sy1 = st.rows;
+  st.sx0 = 0;
+  st.sx1 = SWc;
+  return st;
+}
+
 // Ring copy for every grid of a run in one launch: block (g, d) copies the
 // ring of grid g's input to its buffer d (1 = workspace, 2 = output).
 template <typename T>
@@ -1552,6 +1588,19 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
         fence_proxy_async_global();
       }
       grid_barrier(kp, epoch);
+    } else if (MODE == MODE_GROUPS) {
+      // every wave is all k steps of its grids; the barrier after it also
+      // keeps the next wave's edges out of mailboxes still being read
+      const size_t nslots = (size_t)gridDim.x * kWarps;
+      for (int wv = 0; wv < kp.njobs; ++wv, ++seq) {
+        const Strip st = slot_strip(kp.jobs + ((size_t)wv * nslots + slot) * kSlotInts, SWc);
+        run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        if (lane == 0) {
+          bulk_wait_all();
+          fence_proxy_async_global();
+        }
+        grid_barrier(kp, epoch);
+      }
     } else if (MODE == MODE_BANDS) {
       for (int wv = 0; wv < kp.njobs; ++wv, ++seq) {
         const Strip st = band_strip(kp, kp.jobs + 5 * wv, slot, SWc);
@@ -1635,6 +1684,103 @@ static bool resident_fit(const GridDesc &g, int sw, int ctas, int rmax, int *m_o
   return true;
 }
 
+// Grouped resident (RESIDENT on a batch): every grid must fit the CTAs'
+// warps by itself with strips of at most rmax rows.
+static bool groups_fit(const std::vector<GridDesc> &grids, int sw, int ctas, int rmax) {
+  const long slots = (long)ctas * kWarps;
+  for (const GridDesc &g : grids)
+    if ((long)((g.nx + sw - 1) / sw) * ((g.ny + rmax - 1) / rmax) > slots) return false;
+  return true;
+}
+
+// The waves of a grouped-resident run, as kSlotInts records per slot and
+// wave.  Grids are taken tallest strips first (then most strips) and each
+// goes into the first wave with room for it (first fit, strips of rmax
+// rows); then every wave takes the shortest strip height that still fits
+// its grids, so an under-filled wave spreads over all warps (a wave lasts
+// as long as its tallest strip: warps advance in step with their
+// neighbours).  A grid's strips take consecutive slots, four strip
+// columns at a time row by row, so that a CTA's 16 slots hold 4 x 4 strips
+// and most links stay inside the CTA.  Returns the number of waves (0: a
+// grid does not fit).
+static int group_waves(const std::vector<GridDesc> &grids, int sw, int ctas, int rmax, std::vector<int> &jobs) {
+  const int slots = ctas * kWarps;
+  const int ng = (int)grids.size();
+  if (!groups_fit(grids, sw, ctas, rmax)) return 0;
+  std::vector<int> ncs(ng), order(ng);
+  auto height = [&](int g, int h) {  // strip rows of grid g with strips of at most h rows
+    const int m = (grids[g].ny + h - 1) / h;
+    return (grids[g].ny + m - 1) / m;
+  };
+  auto strips = [&](int g, int h) { return (long)ncs[g] * ((grids[g].ny + h - 1) / h); };
+  for (int g = 0; g < ng; ++g) {
+    ncs[g] = (grids[g].nx + sw - 1) / sw;
+    order[g] = g;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ha = height(a, rmax), hb = height(b, rmax);
+    return ha != hb ? ha > hb : strips(a, rmax) > strips(b, rmax);
+  });
+  std::vector<std::vector<int>> waves;
+  std::vector<long> used;
+  for (int g : order) {
+    const long n = strips(g, rmax);
+    size_t w = 0;
+    while (w < waves.size() && used[w] + n > slots) ++w;
+    if (w == waves.size()) {
+      waves.emplace_back();
+      used.push_back(0);
+    }
+    waves[w].push_back(g);
+    used[w] += n;
+  }
+  const int nw = (int)waves.size();
+  jobs.assign((size_t)nw * slots * kSlotInts, 0);
+  for (size_t i = 0; i < jobs.size(); i += kSlotInts) jobs[i] = -1;
+  for (int w = 0; w < nw; ++w) {
+    int h = 1;
+    for (;; ++h) {
+      long need = 0;
+      for (int g : waves[w]) need += strips(g, h);
+      if (need <= slots || h == rmax) break;
+    }
+    int s0 = 0;
+    for (int g : waves[w]) {
+      const GridDesc &gd = grids[g];
+      const int nc = ncs[g], m = (gd.ny + h - 1) / h;
+      // slot of strip column j, strip row i: groups of four columns, row-major inside a group
+      auto slot_of = [&](int j, int i) {
+        const int grp = j / 4, cw = std::min(4, nc - 4 * grp);
+        return s0 + grp * 4 * m + i * cw + (j - 4 * grp);
+      };
+      const int bsz = gd.ny / m, extra = gd.ny % m;
+      for (int j = 0; j < nc; ++j)
+        for (int i = 0; i < m; ++i) {
+          // rows spread as in the bands: strip i takes one of the leftover rows when floor(i*extra/m) steps up
+          const int before = (int)((long)i * extra / m), upto = (int)((long)(i + 1) * extra / m);
+          const int rows = bsz + (upto - before), y0 = 1 + i * bsz + before, x0 = 1 + j * sw;
+          int ring = 0;
+          if (y0 == 1) ring |= 1 << SIDE_YM;
+          if (y0 + rows - 1 == gd.ny) ring |= 1 << SIDE_YP;
+          if (x0 == 1) ring |= 1 << SIDE_XM;
+          if (gd.nx <= x0 + sw - 1) ring |= 1 << SIDE_XP;
+          int *rec = &jobs[((size_t)w * slots + slot_of(j, i)) * kSlotInts];
+          rec[0] = g;
+          rec[1] = x0;
+          rec[2] = y0;
+          rec[3] = rows;
+          rec[4] = ring;
+          rec[5 + SIDE_YM] = i > 0 ? slot_of(j, i - 1) : LINK_CONST;
+          rec[5 + SIDE_YP] = i < m - 1 ? slot_of(j, i + 1) : LINK_CONST;
+          rec[5 + SIDE_XM] = j > 0 ? slot_of(j - 1, i) : LINK_CONST;
+          rec[5 + SIDE_XP] = j < nc - 1 ? slot_of(j + 1, i) : LINK_CONST;
+        }
+      s0 += nc * m;
+    }
+  }
+  return nw;
+}
+
 // Strips per column for one grid of ncs strip columns on `ctas` CTAs when
 // each CTA holds a block of bx columns x 16/bx rows of strips (bx = 0:
 // consecutive slots run down the columns); 0 if the grid is too wide.
@@ -1672,10 +1818,11 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   int algo = rq.algo;
   const bool single = grids.size() == 1;
   int m = 0;
-  const bool fits = single && resident_fit(grids[0], sw, c.ctas, c.rows, &m);
+  const bool fits = single ? resident_fit(grids[0], sw, c.ctas, c.rows, &m)
+                           : !rq.adjoint && groups_fit(grids, sw, c.ctas, c.rows);
   if (algo == J2D_ALGO_AUTO) {
     if (rq.steps < 4) algo = J2D_ALGO_ONESTEP;
-    else if (fits) algo = J2D_ALGO_RESIDENT;
+    else if (fits && (single || dt == J2D_F64)) algo = J2D_ALGO_RESIDENT;  // FP64 batches: grouped resident
     else algo = J2D_ALGO_TILES;
   }
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
@@ -1788,6 +1935,7 @@ static void *kernel_ptr(int mode, bool adj, int np) {
     if (mode == MODE_TILES_PAIR) return (void *)dtb_kernel<float, false, MODE_TILES_PAIR>;
   }
   if (mode == MODE_SKEW) return np == 9 ? (void *)dtb_kernel<T, false, MODE_SKEW, 9> : (void *)dtb_kernel<T, false, MODE_SKEW>;
+  if (mode == MODE_GROUPS) return (void *)dtb_kernel<T, false, MODE_GROUPS>;  // batches are forward only
   if (mode == MODE_BANDS) return adj ? (void *)dtb_kernel<T, true, MODE_BANDS> : (void *)dtb_kernel<T, false, MODE_BANDS>;
   return adj ? (void *)dtb_kernel<T, true, MODE_TILES> : (void *)dtb_kernel<T, false, MODE_TILES>;
 }
@@ -1807,16 +1955,37 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
                         : pair ? dtb_rows_max_pair(dt, r.smem_optin) : dtb_rows_max(dt, r.smem_optin, kWarps);
   const int rp = (rmax + 3) / 4 * 4;
   if (rmax < 2) { err = "shared memory too small"; return cudaErrorNotSupported; }
-  const int mode = skew ? MODE_SKEW : (r.cfg.algo == J2D_ALGO_TILES) ? MODE_TILES : MODE_BANDS;
   const bool single = grids.size() == 1;
-  if (mode == MODE_BANDS && !single) { err = "bands/resident need a single grid"; return cudaErrorNotSupported; }
+  const int mode = skew ? MODE_SKEW
+                 : (r.cfg.algo == J2D_ALGO_TILES)                ? MODE_TILES
+                 : (r.cfg.algo == J2D_ALGO_RESIDENT && !single) ? MODE_GROUPS
+                                                                 : MODE_BANDS;
+  if (mode == MODE_BANDS && !single) { err = "bands need a single grid"; return cudaErrorNotSupported; }
+  if (mode == MODE_GROUPS && r.adjoint) { err = "batches are forward only"; return cudaErrorNotSupported; }
 
   KParams kp{};
   std::vector<int> jobs, job_off;
   std::vector<long> tkey;
   bool tiles_cached = false;
   int depth = r.cfg.depth, rounds = 1, last = (int)r.steps;
-  if (r.cfg.algo == J2D_ALGO_RESIDENT) {
+  if (mode == MODE_GROUPS) {
+    depth = last = (int)r.steps;
+    rounds = 1;
+    tkey = {ctas, rmax, (long)grids.size(), 2000};
+    for (const GridDesc &g : grids) {
+      tkey.push_back(g.nx);
+      tkey.push_back(g.ny);
+    }
+    tiles_cached = tkey == S.tiles_key;
+    if (tiles_cached) {
+      jobs = S.tiles_jobs;
+    } else {
+      if (group_waves(grids, SW, ctas, rmax, jobs) == 0) { err = "a grid of the batch does not fit on chip"; return cudaErrorNotSupported; }
+      S.tiles_key = tkey;
+      S.tiles_jobs = jobs;
+      S.tiles_off.clear();
+    }
+  } else if (r.cfg.algo == J2D_ALGO_RESIDENT) {
     int m = 0;
     if (!resident_fit(grids[0], SW, ctas, rmax, &m)) { err = "grid does not fit on chip"; return cudaErrorNotSupported; }
     kp.bx = choose_bx((grids[0].nx + SW - 1) / SW, grids[0].ny, ctas, &m);
@@ -1954,7 +2123,8 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
       kp.tile_rows = trows;
     }
   }
-  const int njobs = (int)(jobs.size() / (mode == MODE_BANDS ? 5 : mode == MODE_SKEW ? kSkewInts : kTileInts));
+  const int njobs = mode == MODE_GROUPS ? (int)(jobs.size() / ((size_t)ctas * kWarps * kSlotInts))
+                                        : (int)(jobs.size() / (mode == MODE_BANDS ? 5 : mode == MODE_SKEW ? kSkewInts : kTileInts));
   // TILES: tiles are packed into groups of at most 16 strips that one CTA runs
   // side by side (a tile keeps only its strips inside the grid, so the small
   // tiles of a batch share CTAs instead of leaving warps idle): largest tiles
@@ -2074,7 +2244,8 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   const size_t skew_bytes = mode == MODE_SKEW ? (size_t)ctas * 2 * (depth + 1) * 2 * skew_tw * elem : 0;
   const size_t skew_off = (256 + nslots * sizeof(int) + 255) / 256 * 256;
   const size_t scratch = mode == MODE_SKEW ? skew_off + skew_bytes
-                                           : 256 + nslots * sizeof(int) + (mode == MODE_BANDS ? nslots * slot_bytes : 0);
+                                           : 256 + nslots * sizeof(int) +
+                                                 (mode == MODE_BANDS || mode == MODE_GROUPS ? nslots * slot_bytes : 0);
   ensure(S.scratch, S.scratch_bytes, scratch, e);
   if (e != cudaSuccess) { err = "scratch allocation"; return cudaErrorMemoryAllocation; }
   // upload the descriptors unless the device copy already holds them (a run
@@ -2150,6 +2321,9 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   // CTA block
   kp.mute_slot = r.mute_slot < 0 ? -1 : (kp.bx > 0 ? kp.bx - 1 : 0);
   kp.int_path = r.int_path;
+  kp.dead_all = 0;
+  if (mode == MODE_BANDS || mode == MODE_GROUPS)
+    for (const GridDesc &g : grids) kp.dead_all |= g.nx % SW != 0;
   if (mode == MODE_SKEW) {
     kp.skewbuf = sc + skew_off;
     kp.skew_tw = (int)skew_tw;

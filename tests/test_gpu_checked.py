@@ -82,3 +82,47 @@ def test_checked_box(chk, nx, ny, algo):
     w = synth.box_weights(3201)
     got = _run_checked(chk, u0, w, 6, algo, 3, 4, box=True)
     assert rel_err(got, oracle.box_run(u0, w, 6)) <= TOL_F64
+
+
+def _run_checked_batch(lib, sizes, steps, algo, depth, wx, ctas):
+    import torch
+    n = len(sizes)
+    nx = np.array([s[0] for s in sizes], dtype=np.int32)
+    ny = np.array([s[1] for s in sizes], dtype=np.int32)
+    w = np.stack([synth.weights(3300 + i) for i in range(n)])
+    us = [synth.field(a, b, 3400 + i) for i, (a, b) in enumerate(sizes)]
+    h = ctypes.c_void_p()
+    _status(lib, lib.j2d5pt_plan_batched(ctypes.byref(h), n, nx.ctypes.data_as(ctypes.c_void_p),
+                                         ny.ctypes.data_as(ctypes.c_void_p), j2d5pt.J2D_F64,
+                                         np.ascontiguousarray(w).ctypes.data_as(ctypes.c_void_p)))
+    try:
+        for opt, v in (("algo", j2d5pt.ALGO[algo]), ("depth", depth), ("tile_wx", wx), ("ctas", ctas)):
+            _status(lib, lib.j2d5pt_set_option(h, j2d5pt.OPT[opt], v))
+        srcs, dsts, offs = [], [], []
+        for i, ((a, b), u) in enumerate(zip(sizes, us)):
+            pitch, off = ctypes.c_long(), ctypes.c_long()
+            _status(lib, lib.j2d5pt_layout(h, i, ctypes.byref(pitch), ctypes.byref(off)))
+            src = torch.zeros((b + 2, pitch.value), dtype=torch.float64, device="cuda")
+            src[:, off.value:off.value + a + 2] = torch.from_numpy(u)
+            srcs.append(src)
+            dsts.append(torch.zeros_like(src))
+            offs.append(off.value)
+        pin = (ctypes.c_void_p * n)(*[t.data_ptr() for t in srcs])
+        pout = (ctypes.c_void_p * n)(*[t.data_ptr() for t in dsts])
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _status(lib, lib.j2d5pt_run_batched(h, ctypes.cast(pin, ctypes.c_void_p), ctypes.cast(pout, ctypes.c_void_p),
+                                            steps, stream))
+        _status(lib, lib.j2d5pt_sync_status(h))
+        outs = [d[:, o:o + a + 2].cpu().numpy() for d, o, (a, _) in zip(dsts, offs, sizes)]
+        return us, w, outs
+    finally:
+        lib.j2d5pt_plan_destroy(h)
+
+
+@pytest.mark.parametrize("algo,depth,wx,ctas", [("tiles", 3, 2, 0), ("skewed", 3, 4, 0), ("resident", 0, 0, 0),
+                                                ("resident", 0, 0, 2)])
+def test_checked_batched(chk, algo, depth, wx, ctas):
+    sizes = [(1, 1), (13, 17), (127, 31), (70, 3), (3, 70), (129, 40)]
+    us, w, outs = _run_checked_batch(chk, sizes, 7, algo, depth, wx, ctas)
+    for u, wi, got in zip(us, w, outs):
+        assert rel_err(got, oracle.run(u, wi, 7)) <= TOL_F64, algo
