@@ -295,6 +295,10 @@ struct RingAcc {
   T W, E, S, N;
 };
 
+// Dead cells (strip columns beyond the grid) of FP64 sweeps are skipped
+// rather than evaluated and discarded (see sweep_row).
+template <typename T> constexpr bool kSkipDead = sizeof(T) == 8;
+
 // One row r of a strip sweep: new values of row r from the old rows r-1 (ra),
 // r (rb) and r+1 (rc), stored in place, then the window moves down a row.
 template <typename T, bool ADJ, bool DEAD>
@@ -312,9 +316,10 @@ __device__ __forceinline__ void sweep_row(T (&ra)[VecOf<T>::V], T (&rb)[VecOf<T>
   T o[V];
 #pragma unroll
   for (int e = 0; e < V; ++e) {
-    // a dead cell keeps its value and is not evaluated (its zero-filled
-    // neighbours would send it off the FP64 integer path onto the FMA chain)
-    if (DEAD && (dead & (1u << e))) {
+    // an FP64 dead cell keeps its value and is not evaluated (its zero-filled
+    // neighbours would send it off the integer path onto the FMA chain); FP32
+    // selects after evaluating (skipping measured slower there)
+    if (kSkipDead<T> && DEAD && (dead & (1u << e))) {
       o[e] = rb[e];
       continue;
     }
@@ -323,6 +328,11 @@ __device__ __forceinline__ void sweep_row(T (&ra)[VecOf<T>::V], T (&rb)[VecOf<T>
       o[e] = stencil_cell(a, u, exact_cell(xl + e, y0 + r, ipath), xm, xp, ra[e], rb[e], rc[e]);
     else
       o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
+  }
+  if constexpr (!kSkipDead<T> && DEAD) {
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      if (dead & (1u << e)) o[e] = rb[e];
   }
   vstore(drow + r * SW, o);
 #pragma unroll
@@ -740,7 +750,7 @@ __device__ __forceinline__ void row_update(const T (&ra)[VecOf<T>::V], const T (
   if (lane == 31) right = hr;
 #pragma unroll
   for (int e = 0; e < V; ++e) {
-    if (DEAD && (dead & (1u << e))) {  // dead cells keep their value, unevaluated (as in sweep_row)
+    if (kSkipDead<T> && DEAD && (dead & (1u << e))) {  // as in sweep_row
       o[e] = rb[e];
       continue;
     }
@@ -749,6 +759,11 @@ __device__ __forceinline__ void row_update(const T (&ra)[VecOf<T>::V], const T (
       o[e] = stencil_cell(a, u, exact_cell(xl + e, y, ipath), xm, xp, ra[e], rb[e], rc[e]);
     else
       o[e] = stencil(a, xm, xp, ra[e], rb[e], rc[e]);
+  }
+  if constexpr (!kSkipDead<T> && DEAD) {
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      if (dead & (1u << e)) o[e] = rb[e];
   }
 }
 
@@ -1147,7 +1162,7 @@ __device__ __forceinline__ void sweep_skew_box(T *drow, const T *hct, int rows, 
     const int y = yb + r;
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-      if (DEAD && (dead & (1u << e))) {  // dead cells keep their value, unevaluated (as in sweep_row)
+      if (kSkipDead<T> && DEAD && (dead & (1u << e))) {  // as in sweep_row
         o[e] = rb[e];
         continue;
       }
@@ -1155,6 +1170,7 @@ __device__ __forceinline__ void sweep_skew_box(T *drow, const T *hct, int rows, 
       const T c0 = e == 0 ? bl : rb[e - 1], c2 = e == V - 1 ? br : rb[e + 1];
       const T p0 = e == 0 ? cl : rc[e - 1], p2 = e == V - 1 ? cr : rc[e + 1];
       o[e] = stencil_box_cell(b, u, exact_cell(xl + e, y, ip), m0, ra[e], m2, c0, rb[e], c2, p0, rc[e], p2);
+      if (!kSkipDead<T> && DEAD && (dead & (1u << e))) o[e] = rb[e];
     }
     vstore(drow + r * SW, o);
     shift();
