@@ -161,7 +161,8 @@ j2d_status j2d5pt_run_batched(j2d5pt_plan_t plan, const void *const *in, void *c
 /* End-to-end form on HOST buffers: h_in and h_out are dense (ny+2) x (nx+2)
  * row-major host arrays (ring included).  Copies in, runs, copies out and
  * synchronises; uses the plan's device workspace.  Pinned host memory gives
- * full copy bandwidth. */
+ * full copy bandwidth: a pinned h_in is read by a gather kernel on the device
+ * (pageable memory takes a plain copy). */
 j2d_status j2d5pt_run_host(j2d5pt_plan_t plan, const void *h_in, void *h_out, long steps);
 
 /* ---- adjoint and gradient (the transpose of the forward map) ------------ */

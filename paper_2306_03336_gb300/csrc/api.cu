@@ -528,8 +528,19 @@ extern "C" j2d_status j2d5pt_run_host(j2d5pt_plan_t p, const void *h_in, void *h
   cudaStream_t s = nullptr;
   const size_t w = (size_t)(g.nx + 2) * p->elem, dp = (size_t)g.pitch * p->elem;
   char *din = (char *)p->h_in_dev + g.off * p->elem, *dout = (char *)p->h_out_dev + g.off * p->elem;
-  if ((e = cudaMemcpy2DAsync(din, dp, h_in, w, w, g.ny + 2, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  // pinned (device-accessible) input: gathered by a kernel; otherwise one 2D copy
+  cudaPointerAttributes pa{};
+  const void *h_dev = nullptr;
+  if (cudaPointerGetAttributes(&pa, h_in) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+    h_dev = pa.devicePointer;
+  else
+    cudaGetLastError();  // clear a failed query
+  if (h_dev) {
+    if ((e = launch_gather_rows(p->dtype, h_dev, g.nx + 2, din, g.pitch, g.ny + 2, g.nx + 2, s)) != cudaSuccess)
+      return cuda_fail(e, "run_host: gather in");
+  } else if ((e = cudaMemcpy2DAsync(din, dp, h_in, w, w, g.ny + 2, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
     return cuda_fail(e, "run_host: copy in");
+  }
   j2d_status st = j2d5pt_run(p, p->h_in_dev, p->h_out_dev, steps, s);
   if (st != J2D_OK) return st;
   if ((e = cudaMemcpy2DAsync(h_out, w, dout, dp, w, g.ny + 2, cudaMemcpyDeviceToHost, s)) != cudaSuccess)

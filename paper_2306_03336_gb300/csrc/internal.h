@@ -66,6 +66,10 @@ cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *d
                          const GridDesc &g, cudaStream_t s);
 cudaError_t launch_adjoint_wgrad(j2d_dtype dt, const void *u, const void *lam1, void *lam0, double *dw,
                                  double *partials, long max_partials, const GridDesc &g, int ipath, cudaStream_t s);
+// rows x width elements from src (row stride spitch; device-accessible, e.g.
+// pinned host memory) to dst (row stride dpitch)
+cudaError_t launch_gather_rows(j2d_dtype dt, const void *src, long spitch, void *dst, long dpitch, long rows, long width,
+                               cudaStream_t s);
 cudaError_t measure_fma(j2d_dtype dt, double *rate);
 cudaError_t measure_exact(double *rate);
 cudaError_t measure_exact_box(double *rate);

@@ -195,6 +195,28 @@ def test_run_host_end_to_end_matches_device_run():
     assert rel_err(host, oracle.run(u0, w, steps)) <= TOL_F64
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("nx,ny", [(300, 200), (1, 1), (7, 13), (1023, 5), (129, 257)])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_run_host_pinned_and_pageable(dtype, nx, ny, pinned):
+    """A pinned input is gathered on the device by a kernel, a pageable one
+    copied; odd row lengths leave the host rows unaligned to 16 bytes.  Both
+    give the device run's bits, and 0 steps give the input back."""
+    import torch
+    u0 = synth.field(nx, ny, 63 + nx).astype(np.float64 if dtype == "f64" else np.float32)
+    w = synth.weights(64)
+    p = j2d5pt.Plan(nx, ny, dtype, w)
+    src = torch.from_numpy(u0).pin_memory().numpy() if pinned else u0.copy()
+    out = torch.empty(u0.shape, dtype=p.torch_dtype).pin_memory().numpy() if pinned else None
+    assert np.array_equal(p.run_host(src, 0, out=out), u0)
+    host = p.run_host(src, 9, out=out).copy()
+    d_in = p.to_device(u0)
+    d_out = p.empty()
+    p.run(d_in, d_out, 9)
+    assert np.array_equal(host, p.to_host(d_out))
+    p.close()
+
+
 def test_argument_errors_on_device():
     import torch
     p = j2d5pt.Plan(64, 64, "f64", synth.weights(1))
