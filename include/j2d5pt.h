@@ -165,6 +165,21 @@ j2d_status j2d5pt_run_batched(j2d5pt_plan_t plan, const void *const *in, void *c
  * (pageable memory takes a plain copy). */
 j2d_status j2d5pt_run_host(j2d5pt_plan_t plan, const void *h_in, void *h_out, long steps);
 
+/* Forward run that keeps every intermediate state (the recomputation of a
+ * checkpointed gradient): `states` is a device buffer of `steps` consecutive
+ * grids in the plan layout, each (ny+2) * pitch elements, 16-byte aligned;
+ * state t (1 <= t <= steps, ring included) is written at states + (t-1) *
+ * (ny+2) * pitch elements.  Bit-identical to `steps` chained calls of
+ * j2d5pt_run(plan, ., ., 1, stream).  With J2D_ALGO_AUTO the one-step
+ * kernel runs one launch per state (it writes every state anyway, and
+ * measured faster than blocked kernels storing each step); a plan set to a
+ * temporally blocked algorithm stores each state from its one persistent
+ * launch (the skewed and two-step FP32 schedules run as single-step tiles
+ * here).  Single-grid, five-point plans; `in` must not lie
+ * inside `states`; steps >= 1.  J2D_ERR_ARG / J2D_ERR_ALIGN /
+ * J2D_ERR_UNSUPPORTED as for j2d5pt_run. */
+j2d_status j2d5pt_run_states(j2d5pt_plan_t plan, const void *in, void *states, long steps, void *stream);
+
 /* ---- adjoint and gradient (the transpose of the forward map) ------------ */
 
 /* lam_0 = (M^T)^steps lam_T, where M is one forward step over all cells

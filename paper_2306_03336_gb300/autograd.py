@@ -12,8 +12,8 @@ its update, Section 3.1, Listing 1):
 The map is linear in u for fixed weights, so dL/du_0 needs no forward states
 and is one adjoint run.  The weight gradient needs every u_t: the forward keeps
 a checkpoint every `checkpoint` steps, and the backward recomputes one
-segment at a time from its checkpoint (keeping that segment's states) and
-walks it in reverse.  Memory: steps/checkpoint + checkpoint grid copies
+segment at a time from its checkpoint, every state of it kept by one
+state-keeping run (j2d5pt_run_states), and walks it in reverse.  Memory: steps/checkpoint + checkpoint grid copies
 instead of steps.
 
 Layout plumbing (copies between dense (ny+2, nx+2) tensors and the plan's
@@ -35,10 +35,12 @@ class J2D5PT:
         self.nx, self.ny, self.dtype, self.checkpoint = int(nx), int(ny), dtype, int(checkpoint)
         self.plan = j2d5pt.Plan(nx, ny, dtype, np.full(5, 0.2))
         self._pool = []
+        self._states = None
 
     def close(self):
         self.plan.close()
         self._pool = []
+        self._states = None
 
     @property
     def torch_dtype(self):
@@ -48,6 +50,12 @@ class J2D5PT:
         while len(self._pool) <= i:
             self._pool.append(self.plan.empty())
         return self._pool[i]
+
+    def _segment_states(self):
+        # states 1 .. checkpoint-1 of a segment, one contiguous buffer
+        if self._states is None and self.checkpoint > 1:
+            self._states = self.plan.empty_states(self.checkpoint - 1)
+        return self._states
 
     def _set_weights(self, w):
         self.plan.set_weights(w.detach().to("cpu", torch.float64).numpy())
@@ -96,10 +104,12 @@ class _J2D5PTFn(torch.autograd.Function):
             nseg = len(cks)
             for j in reversed(range(nseg)):
                 n = min(c, steps - j * c)
-                # recompute this segment's states u_{jc} .. u_{jc+n-1}
-                states = [cks[j]] + [op._buf(3 + i) for i in range(n - 1)]
-                for i in range(n - 1):
-                    plan.run(states[i], states[i + 1], 1)
+                # recompute this segment's states u_{jc} .. u_{jc+n-1} in one run
+                states = [cks[j]]
+                if n > 1:
+                    buf = op._segment_states()
+                    plan.run_states(cks[j], buf[:n - 1], n - 1)
+                    states += [buf[i] for i in range(n - 1)]
                 for t in reversed(range(n)):
                     # lam holds lam_{t+1}: one pass gives lam_t and the step's dL/dw
                     plan.adjoint_step_wgrad(states[t], lam, tmp, dw)

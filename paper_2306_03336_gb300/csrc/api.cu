@@ -356,6 +356,9 @@ static j2d_status run_grid_onestep(j2d5pt_plan_t p, int gi, const void *in, void
   return J2D_OK;
 }
 
+static j2d_status run_dtb(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps, bool adj,
+                          const DtbConfig &c, cudaStream_t s, void *states = nullptr, long state_elems = 0);
+
 static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps, bool adj,
                              cudaStream_t s) {
   if (steps < 0) return fail(J2D_ERR_ARG, "run: steps %ld < 0", steps);
@@ -379,6 +382,13 @@ static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const
     }
     return J2D_OK;
   }
+  return run_dtb(p, in, out, steps, adj, c, s);
+}
+
+// One temporally blocked launch (with its set-up) for a resolved configuration;
+// `states` (one grid, forward) keeps every state, `state_elems` apart.
+static j2d_status run_dtb(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps, bool adj,
+                          const DtbConfig &c, cudaStream_t s, void *states, long state_elems) {
   std::vector<void *> wsv;
   for (size_t i = 0; i < p->grids.size(); ++i) wsv.push_back(ws_of(p, (int)i));
   DtbRun r;
@@ -390,6 +400,8 @@ static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const
   r.steps = steps;
   r.adjoint = adj;
   r.cfg = c;
+  r.states = states;
+  r.state_elems = state_elems;
   r.status = p->d_status;
   r.timeout_ns = (unsigned long long)p->opt_timeout_ms * 1000000ull;
   r.mute_slot = p->opt_fault ? 0 : -1;
@@ -546,6 +558,57 @@ extern "C" j2d_status j2d5pt_run_host(j2d5pt_plan_t p, const void *h_in, void *h
   if ((e = cudaMemcpy2DAsync(h_out, w, dout, dp, w, g.ny + 2, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(e, "run_host: copy out");
   return j2d5pt_sync_status(p);
+}
+
+extern "C" j2d_status j2d5pt_run_states(j2d5pt_plan_t p, const void *in, void *states, long steps, void *stream) {
+  if (!p || !in || !states) return fail(J2D_ERR_ARG, "run_states: null argument");
+  if (p->grids.size() != 1) return fail(J2D_ERR_ARG, "run_states: single-grid plans only");
+  if (is_box(p)) return fail(J2D_ERR_UNSUPPORTED, "run_states: five-point plans only");
+  if (steps < 1) return fail(J2D_ERR_ARG, "run_states: steps must be >= 1");
+  if (!aligned16(in) || !aligned16(states)) return fail(J2D_ERR_ALIGN, "run_states: buffer not 16-byte aligned");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != p->device) return fail(J2D_ERR_DEVICE, "run_states: current device %d differs from the plan's device %d", cur, p->device);
+  const GridDesc &g = p->grids[0];
+  const long se = (long)(g.ny + 2) * g.pitch;  // elements per state
+  const size_t sb = (size_t)se * p->elem;
+  char *st0 = (char *)states;
+  if ((const char *)in >= st0 && (const char *)in < st0 + sb * (size_t)steps)
+    return fail(J2D_ERR_ARG, "run_states: in lies inside states");
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  p->ran = true;
+  cudaError_t e;
+  if ((e = launch_ring_copy(p->dtype, in, states, g, s, steps, se)) != cudaSuccess) return cuda_fail(e, "run_states: rings");
+  // AUTO keeps the states with the one-step kernel, which writes every state
+  // anyway: FP64 4096^2, 49 states, 6.48 ms against 6.81 for tiles storing
+  // each step (the stores cost the tiled sweep 18%)
+  DtbConfig c = resolve(p, steps, false);
+  if (p->opt_algo == J2D_ALGO_AUTO) c.algo = J2D_ALGO_ONESTEP;
+  if (c.algo == J2D_ALGO_ONESTEP) {
+    const void *src = in;
+    for (long t = 0; t < steps; ++t) {
+      void *dst = st0 + (size_t)t * sb;
+      if ((e = launch_onestep(p->dtype, false, src, dst, g, int_path_of(p), s)) != cudaSuccess)
+        return cuda_fail(e, "run_states: one-step launch");
+      src = dst;
+    }
+    return J2D_OK;
+  }
+  if (c.algo == J2D_ALGO_SKEWED || c.sweep == 2) {
+    // the skewed and two-step sweeps hold no whole state of a strip between
+    // their steps: single-step tiles (the plan's depth and shape if it chose tiles)
+    DtbRequest rq;
+    rq.algo = J2D_ALGO_TILES;
+    rq.depth = c.algo == J2D_ALGO_TILES ? p->opt_depth : 0;
+    rq.tile_wx = c.algo == J2D_ALGO_TILES ? p->opt_tile_wx : 0;
+    rq.ctas = p->opt_ctas;
+    rq.steps = steps;
+    rq.sweep_steps = 1;
+    c = dtb_choose(p->dtype, p->grids, p->sms, p->smem_optin, rq);
+  }
+  void *last = st0 + (size_t)(steps - 1) * sb;
+  return run_dtb(p, &in, &last, steps, false, c, s, states, se);
 }
 
 extern "C" j2d_status j2d5pt_sync_status(j2d5pt_plan_t p) {

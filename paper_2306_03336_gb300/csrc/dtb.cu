@@ -113,6 +113,8 @@ struct KParams {
   void *skewbuf;            // SKEWED: per CTA [2 parities][levels][2 rows][skew_tw] elements
   int skew_tw, skew_levels, skew_wx;  // SKEWED: band width (elements), levels per parity, strips across
   int dead_all;             // RESIDENT / BANDS, FP64: some strip has dead columns, all take the dead-column sweep
+  void *states;             // forward runs keeping every state: state t+1 at states + t * state_elems (or null)
+  long state_elems;
 };
 
 // Layout of one warp's shared-memory region (elements of T).
@@ -486,9 +488,35 @@ __device__ void strip_store(const Strip &st, const GridDev &gd, const T *data, c
 // scope for a neighbour in another CTA), waited for only by the strips that
 // border it; for FP32, neighbours in the same CTA are ordered by one CTA
 // barrier per step instead.
+// The valid cells of a strip (its rows [sy0, sy1) and columns [sx0, sx1)
+// inside the grid) into the grid-shaped buffer `out`: a 16-byte store per
+// lane and row where the lane's whole vector is valid, single elements where
+// it is not.  Used for the intermediate states of a state-keeping run.
+template <typename T>
+__device__ void strip_store_plain(const Strip &st, const GridDev &gd, const T *drow, int lane, T *out) {
+  constexpr int V = VecOf<T>::V;
+  constexpr int SW = 32 * V;
+  const int c0 = lane * V, xe = gd.nx - st.x0;  // last valid strip column
+  const bool whole = c0 >= st.sx0 && c0 + V <= st.sx1 && c0 + V - 1 <= xe;
+  for (int r = st.sy0; r < st.sy1; ++r) {
+    T *row = out + (long)(st.y0 + r) * gd.pitch + gd.off + st.x0;
+    if (whole) {
+      T v[V];
+      vload(drow + r * SW, false, v);
+      vstore(row + c0, v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const int c = c0 + e;
+        if (c >= st.sx0 && c < st.sx1 && c <= xe) stm(&row[c], ldm(&drow[r * SW + e]));
+      }
+    }
+  }
+}
+
 template <typename T, bool ADJ>
 __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int warp, int slot, int src, int dst,
-                          int k, int base, uint32_t &mbar_phase, const Prefetch &pf = Prefetch{}) {
+                          int k, int base, uint32_t &mbar_phase, const Prefetch &pf = Prefetch{}, int step0 = 0) {
   constexpr int V = VecOf<T>::V;
   constexpr int SW = 32 * V;
   using L = WarpLayout<T>;
@@ -709,6 +737,8 @@ __device__ void run_strip(const Strip &st, const KParams &kp, char *smem, int wa
       else
         sweep_rows<T, ADJ, false>(drow, hcol, rows, lane, a, u, kp.int_path != 0, xl, st.y0, hym, hyp, dead, rg);
       __syncwarp();
+      if (!ADJ && kp.states)  // a state-keeping run: this step's valid cells into their state
+        strip_store_plain<T>(st, gd, drow, lane, reinterpret_cast<T *>(kp.states) + (size_t)(step0 + t) * kp.state_elems);
       publish_edges(par ^ 1);
       publish_local(base + t + 1);
       publish_remote(base + t + 1);
@@ -1620,7 +1650,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
     } else if (MODE == MODE_BANDS) {
       for (int wv = 0; wv < kp.njobs; ++wv, ++seq) {
         const Strip st = band_strip(kp, kp.jobs + 5 * wv, slot, SWc);
-        run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase);
+        run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase, Prefetch{}, r * kp.depth);
         if (lane == 0) {
           bulk_wait_all();
           fence_proxy_async_global();
@@ -1647,7 +1677,7 @@ __global__ void __launch_bounds__(kThreads, 1) dtb_kernel(const __grid_constant_
               pf.y = nst.y0;
             }
           }
-          run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase, pf);
+          run_strip<T, ADJ>(st, kp, smem, warp, slot, src, dst, k, seq * kmax1, phase, pf, r * kp.depth);
         }
         __syncthreads();
       }
@@ -1978,6 +2008,10 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
                                                                  : MODE_BANDS;
   if (mode == MODE_BANDS && !single) { err = "bands need a single grid"; return cudaErrorNotSupported; }
   if (mode == MODE_GROUPS && r.adjoint) { err = "batches are forward only"; return cudaErrorNotSupported; }
+  if (r.states && (r.adjoint || !single || pair || mode == MODE_SKEW || mode == MODE_GROUPS)) {
+    err = "keeping every state needs a forward single-grid run of the single-step strips";
+    return cudaErrorNotSupported;
+  }
 
   KParams kp{};
   std::vector<int> jobs, job_off;
@@ -2292,6 +2326,7 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
     for (int b = 0; b < 3; ++b) span(hg[i].buf[b], grids[i].bytes(elem));
   span(S.scratch, scratch);
   span(S.desc, desc_bytes);
+  if (r.states) span(r.states, (size_t)r.steps * (size_t)r.state_elems * elem);
   kp.mem_lo = mem_lo;
   kp.mem_hi = mem_hi;
 
@@ -2337,6 +2372,8 @@ cudaError_t dtb_run(DtbState &S, const DtbRun &r, cudaStream_t s, std::string &e
   // CTA block
   kp.mute_slot = r.mute_slot < 0 ? -1 : (kp.bx > 0 ? kp.bx - 1 : 0);
   kp.int_path = r.int_path;
+  kp.states = r.states;
+  kp.state_elems = r.state_elems;
   kp.dead_all = 0;
   if (mode == MODE_BANDS || mode == MODE_GROUPS)
     for (const GridDesc &g : grids) kp.dead_all |= g.nx % SW != 0;

@@ -37,6 +37,8 @@ struct DtbRun {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // recorded around the kernel if set
   int mute_slot = -1;                         // fault injection (J2D_OPT_FAULT_INJECT): >= 0 = on
   int int_path = 0;                           // FP64 integer path on (J2D_OPT_INT_PATH)
+  void *states = nullptr;                     // keep every state: state t+1 at states + t * state_elems (forward,
+  long state_elems = 0;                       // one grid, RESIDENT / BANDS / single-step TILES)
 };
 
 // Device scratch and cached launch data owned by a plan.

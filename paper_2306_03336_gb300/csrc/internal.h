@@ -60,7 +60,9 @@ inline void note_launch(long n = 1) { g_launches.fetch_add(n, std::memory_order_
 
 cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, const GridDesc &g, int ipath,
                            cudaStream_t s);
-cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const GridDesc &g, cudaStream_t s);
+// the ring of `in` into out, or into `count` grids `ostride` elements apart
+cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const GridDesc &g, cudaStream_t s,
+                             long count = 1, long ostride = 0);
 long wgrad_partial_count(j2d_dtype dt, const GridDesc &g);
 cudaError_t launch_wgrad(j2d_dtype dt, const void *u, const void *lam, double *dw, double *partials,
                          const GridDesc &g, cudaStream_t s);

@@ -250,20 +250,24 @@ __global__ void __launch_bounds__(256) onestep_box_kernel(const T *__restrict__ 
 // Copy the ring (rows 0 and ny+1, columns 0 and nx+1) of `in` to `out`.
 template <typename T>
 __global__ void ring_copy_kernel(const T *__restrict__ in, T *__restrict__ out, long pitch, int off, int nx,
-                                 int ny) {
+                                 int ny, long ostride, long count) {
+  // the ring of `in` into `count` outputs `ostride` elements apart (blockIdx.y over outputs)
   const int n_rows = 2 * (nx + 2), n = n_rows + 2 * ny;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int y, x;
-    if (i < n_rows) {
-      y = (i < nx + 2) ? 0 : ny + 1;
-      x = i % (nx + 2);
-    } else {
-      const int j = i - n_rows;
-      y = 1 + (j >> 1);
-      x = (j & 1) ? nx + 1 : 0;
+  for (long c = blockIdx.y; c < count; c += gridDim.y) {
+    T *o = out + c * ostride;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      int y, x;
+      if (i < n_rows) {
+        y = (i < nx + 2) ? 0 : ny + 1;
+        x = i % (nx + 2);
+      } else {
+        const int j = i - n_rows;
+        y = 1 + (j >> 1);
+        x = (j & 1) ? nx + 1 : 0;
+      }
+      const long e = (long)y * pitch + off + x;
+      o[e] = in[e];
     }
-    const long e = (long)y * pitch + off + x;
-    out[e] = in[e];
   }
 }
 
@@ -502,14 +506,18 @@ cudaError_t launch_onestep(j2d_dtype dt, bool adj, const void *in, void *out, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const GridDesc &g, cudaStream_t s) {
+cudaError_t launch_ring_copy(j2d_dtype dt, const void *in, void *out, const GridDesc &g, cudaStream_t s,
+                             long count, long ostride) {
   const int n = 2 * (g.nx + 2) + 2 * g.ny;
   const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  const dim3 grd((unsigned)blocks, (unsigned)std::min<long>(std::max<long>(count, 1), 1024));
   note_launch();
   if (dt == J2D_F64)
-    ring_copy_kernel<double><<<blocks, 256, 0, s>>>((const double *)in, (double *)out, g.pitch, (int)g.off, g.nx, g.ny);
+    ring_copy_kernel<double><<<grd, 256, 0, s>>>((const double *)in, (double *)out, g.pitch, (int)g.off, g.nx, g.ny,
+                                                 ostride, count);
   else
-    ring_copy_kernel<float><<<blocks, 256, 0, s>>>((const float *)in, (float *)out, g.pitch, (int)g.off, g.nx, g.ny);
+    ring_copy_kernel<float><<<grd, 256, 0, s>>>((const float *)in, (float *)out, g.pitch, (int)g.off, g.nx, g.ny,
+                                                ostride, count);
   return cudaGetLastError();
 }
 

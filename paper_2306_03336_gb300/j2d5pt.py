@@ -76,6 +76,7 @@ def _open(path):
         "j2d5pt_run": [P, P, P, L, P],
         "j2d5pt_run_batched": [P, P, P, L, P],
         "j2d5pt_run_host": [P, P, P, L],
+        "j2d5pt_run_states": [P, P, P, L, P],
         "j2d5pt_run_adjoint": [P, P, P, L, P],
         "j2d5pt_weight_grad": [P, P, P, P, P],
         "j2d5pt_adjoint_step_wgrad": [P, P, P, P, P, P],
@@ -212,6 +213,10 @@ def j2d5pt_run_batched(h, srcs, dsts, steps, stream=None):
 def j2d5pt_run_host(h, h_in, h_out, steps):
     _check(load().j2d5pt_run_host(h, h_in.ctypes.data_as(ctypes.c_void_p), h_out.ctypes.data_as(ctypes.c_void_p),
                                   int(steps)))
+
+
+def j2d5pt_run_states(h, src, states, steps, stream=None):
+    _check(load().j2d5pt_run_states(h, _ptr(src), _ptr(states), int(steps), _stream_ptr(stream)))
 
 
 def j2d5pt_run_adjoint(h, lam_T, lam_0, steps, stream=None):
@@ -397,6 +402,19 @@ class Plan:
         """lam_t = one adjoint step of lam_t1; dw += weight gradient of (u_t, lam_t1)."""
         j2d5pt_adjoint_step_wgrad(self.handle, u_t, lam_t1, lam_t, dw, stream)
         return lam_t
+
+    def empty_states(self, steps):
+        """Zeroed device buffer for `steps` states of grid 0, shape (steps, ny+2, pitch)."""
+        import torch
+        nx, ny = self.sizes[0]
+        pitch, _ = self.layouts[0]
+        return torch.zeros((steps, ny + 2, pitch), dtype=self.torch_dtype, device="cuda")
+
+    def run_states(self, src, states, steps, stream=None):
+        """Every state of a forward run: states[t-1] <- state t, t = 1..steps
+        (states from empty_states or a same-shaped slice of one)."""
+        j2d5pt_run_states(self.handle, src, states, steps, stream)
+        return states
 
     def run_host(self, a, steps, out=None):
         """End to end on host arrays: dense (ny+2, nx+2) in, same shape out

@@ -126,3 +126,33 @@ def test_checked_batched(chk, algo, depth, wx, ctas):
     us, w, outs = _run_checked_batch(chk, sizes, 7, algo, depth, wx, ctas)
     for u, wi, got in zip(us, w, outs):
         assert rel_err(got, oracle.run(u, wi, 7)) <= TOL_F64, algo
+
+
+@pytest.mark.parametrize("algo,depth,wx", [("tiles", 3, 2), ("bands", 3, 0), ("resident", 0, 0)])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (13, 17), (127, 131)])
+def test_checked_states(chk, algo, depth, wx, nx, ny):
+    """The state-keeping run's per-step stores through the checked build."""
+    import torch
+    u0 = synth.field(nx, ny, 3500 + nx)
+    w = synth.weights(3501)
+    steps = 6
+    h = ctypes.c_void_p()
+    wa = np.ascontiguousarray(w, dtype=np.float64)
+    _status(chk, chk.j2d5pt_plan(ctypes.byref(h), nx, ny, j2d5pt.J2D_F64, wa.ctypes.data_as(ctypes.c_void_p)))
+    try:
+        for opt, v in (("algo", j2d5pt.ALGO[algo]), ("depth", depth), ("tile_wx", wx)):
+            _status(chk, chk.j2d5pt_set_option(h, j2d5pt.OPT[opt], v))
+        pitch, off = ctypes.c_long(), ctypes.c_long()
+        _status(chk, chk.j2d5pt_layout(h, 0, ctypes.byref(pitch), ctypes.byref(off)))
+        src = torch.zeros((ny + 2, pitch.value), dtype=torch.float64, device="cuda")
+        src[:, off.value:off.value + nx + 2] = torch.from_numpy(u0)
+        states = torch.zeros((steps, ny + 2, pitch.value), dtype=torch.float64, device="cuda")
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _status(chk, chk.j2d5pt_run_states(h, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(states.data_ptr()),
+                                           steps, stream))
+        _status(chk, chk.j2d5pt_sync_status(h))
+        for t in range(steps):
+            got = states[t, :, off.value:off.value + nx + 2].cpu().numpy()
+            assert rel_err(got, oracle.run(u0, w, t + 1)) <= TOL_F64, (algo, t + 1)
+    finally:
+        chk.j2d5pt_plan_destroy(h)
