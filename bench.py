@@ -299,7 +299,7 @@ def run_ours(args):
     # end to end through the C ABI on host buffers (pinned input and output)
     host_in = torch.from_numpy(u0).pin_memory().numpy()
     host_out = torch.empty(u0.shape, dtype=torch.float64).pin_memory().numpy()
-    t_e2e = []
+    t_e2e, k_e2e = [], []
     n_e2e = max(3, min(args.steps, 5))
     clocks_e2e = Clocks(local)
     clocks_e2e.start()
@@ -311,10 +311,12 @@ def run_ours(args):
         t1 = time.perf_counter()
         if i >= 1:
             t_e2e.append(t1 - t0)
+            k_e2e.append(plan.kernel_time())
     clk_e2e = clocks_e2e.stop()
     e2e = {"value": round(cells * len(t_e2e) * world / sum(t_e2e) / 1e9, 3), "unit": "GCells/s",
            "h2d_bytes_per_step": int(host_in.nbytes), "d2h_bytes_per_step": int(out_h.nbytes),
-           "reps": len(t_e2e), "rep_seconds": [round(t, 4) for t in t_e2e], "clocks": clk_e2e}
+           "reps": len(t_e2e), "rep_seconds": [round(t, 4) for t in t_e2e],
+           "kernel_ms": [round(k, 1) for k in k_e2e], "clocks": clk_e2e}
     del host_in, host_out
 
     extras = {}
@@ -623,7 +625,8 @@ def run_reference(args):
 
 # ---- named runs for profiling --------------------------------------------------
 # name: (nx, ny, dtype, algo, depth, tile_wx, steps, runs); algo "auto" = autotuned,
-# "box:ALGO" = the 3x3 box stencil with that algorithm
+# "box:ALGO" = the 3x3 box stencil with that algorithm, "batch:ALGO" = the first
+# nx grids of the 256-grid batch workload with that algorithm
 WORKLOADS = {
     "headline": (HEAD_N, HEAD_N, "f64", "auto", 0, 0, HEAD_T, 2),
     "f64tiles": (8192, 8192, "f64", "tiles", 4, 4, 8, 1),
@@ -634,6 +637,7 @@ WORKLOADS = {
     "f32skewed": (8192, 8192, "f32", "skewed", 16, 8, 32, 1),
     "f32onestep": (8192, 8192, "f32", "onestep", 0, 0, 4, 1),
     "f64box": (8192, 8192, "f64", "box:skewed", 4, 4, 8, 1),
+    "f64batch": (64, 0, "f64", "batch:resident", 0, 0, 20, 1),
 }
 
 
@@ -647,6 +651,19 @@ def run_workload(name):
     nx, ny, dt, algo, depth, wx, steps, runs = WORKLOADS[name]
     __graft_entry__.build()
     torch.cuda.set_device(0)
+    if algo.startswith("batch:"):
+        cfg = synth.WORKLOADS["j2d5pt_f64_batch256_200"]
+        sizes = synth.batch_sizes(cfg["count"], synth.data_seed(cfg["index"]), cfg["lo"], cfg["hi"])[:nx]
+        ws = np.stack([synth.weights(synth.weight_seed(cfg["index"]) + i) for i in range(len(sizes))])
+        p = j2d5pt.Plan.batch(sizes, dt, ws).set("algo", algo[6:])
+        srcs = [p.to_device(synth.field(a, b, synth.data_seed(cfg["index"]) + 10 + i), i) for i, (a, b) in enumerate(sizes)]
+        dsts = [p.empty(i) for i in range(len(sizes))]
+        for _ in range(runs):
+            p.run_batched(srcs, dsts, steps)
+        p.sync()
+        print(name, p.describe(), flush=True)
+        p.close()
+        return
     if algo.startswith("box:"):
         algo = algo[4:]
         p = j2d5pt.Plan.box9(nx, ny, dt, synth.box_weights(synth.weight_seed(1)))

@@ -630,8 +630,9 @@ extern "C" j2d_status j2d5pt_sync_status(j2d5pt_plan_t p) {
 // Autotuner.  Candidates: the one-step kernel; the resident kernel when the
 // grid fits on chip; bands, tiles and skewed tiles over temporal depths k
 // (and tile shapes).
-// Each is timed with CUDA events for min(steps, 64) steps (best of two runs
-// after a warm-up run); the fastest is kept in the plan.  With J2D_TUNE_CACHE set, results are
+// Each is timed with CUDA events for min(steps, 64) steps, or more when that
+// takes under 5 ms (best of two or three runs after a warm-up run); the
+// fastest per step is kept in the plan.  With J2D_TUNE_CACHE set, results are
 // read from / appended to that file, keyed by device, SM count, dtype, grid
 // sizes and the step-count bucket.
 static std::string tune_key(j2d5pt_plan_t p, long steps) {
@@ -723,23 +724,36 @@ static j2d_status autotune_common(j2d5pt_plan_t p, const void *const *in, void *
     p->opt_algo = c.algo;
     p->opt_depth = c.depth;
     p->opt_tile_wx = c.wx;
-    if (run_common(p, in, out, tsteps, false, s) != J2D_OK || j2d5pt_sync_status(p) != J2D_OK) continue;
+    // warm-up run, timed: a candidate that takes under 5 ms for tsteps is
+    // timed over proportionally more steps (up to `steps`), so that short
+    // runs are not decided by noise; candidates compare by time per step
+    cudaEventRecord(e0, s);
+    if (run_common(p, in, out, tsteps, false, s) != J2D_OK) continue;
+    cudaEventRecord(e1, s);
+    float warm = 0;
+    if (cudaEventSynchronize(e1) != cudaSuccess || j2d5pt_sync_status(p) != J2D_OK ||
+        cudaEventElapsedTime(&warm, e0, e1) != cudaSuccess)
+      continue;
+    long n = tsteps;
+    if (warm < 5.0f && tsteps < steps)
+      n = std::min<long>(steps, (long)std::ceil(tsteps * 5.0 / std::max(warm, 0.05f)));
+    const int nrep = warm < 20.0f ? 3 : 2;  // best of three short runs, two long ones
     float ms = 1e30f;
     bool ok = true;
-    for (int rep = 0; rep < 2 && ok; ++rep) {  // best of two timed runs
+    for (int rep = 0; rep < nrep && ok; ++rep) {
       cudaEventRecord(e0, s);
-      j2d_status st = run_common(p, in, out, tsteps, false, s);
+      j2d_status st = run_common(p, in, out, n, false, s);
       cudaEventRecord(e1, s);
       ok = st == J2D_OK && cudaEventSynchronize(e1) == cudaSuccess && j2d5pt_sync_status(p) == J2D_OK;
       float m = 0;
       if (ok && cudaEventElapsedTime(&m, e0, e1) == cudaSuccess && m < ms) ms = m;
     }
     if (!ok) continue;
+    const float per_step = ms / (float)n;
     if (p->opt_verbose)
-      fprintf(stderr, "[j2d5pt] tune algo=%d depth=%d wx=%d: %.3f ms for %ld steps\n", c.algo, c.depth, c.wx, ms,
-              tsteps);
-    if (ms < best_ms) {
-      best_ms = ms;
+      fprintf(stderr, "[j2d5pt] tune algo=%d depth=%d wx=%d: %.3f ms for %ld steps\n", c.algo, c.depth, c.wx, ms, n);
+    if (per_step < best_ms) {
+      best_ms = per_step;
       best = c;
     }
   }
