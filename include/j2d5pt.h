@@ -68,11 +68,18 @@ typedef enum {
                             steps (every grid must fit on chip by itself) */
   J2D_ALGO_BANDS = 3,    /* GPU-wide bands of the grid, processed serially, k steps per visit */
   J2D_ALGO_TILES = 4,    /* independent per-CTA tiles with a k-deep overlapped halo */
-  J2D_ALGO_SKEWED = 5    /* serial tiles in skewed order: each CTA advances a run of rows of a
+  J2D_ALGO_SKEWED = 5,   /* serial tiles in skewed order: each CTA advances a run of rows of a
                             column band tile after tile, k steps per visit, each tile taking its
                             top halo at every step from the tile before it (no overlapped halo
                             in y; the k-deep overlap stays in x).  Forward runs only (adjoint
                             runs of a plan set to it take TILES). */
+  J2D_ALGO_STREAM = 6    /* temporal blocking in the register file: each warp sweeps a column
+                            band (32 16-byte vectors wide, overlapped halo in x) down a run of
+                            rows, advancing k steps per pass as a pipeline held in registers
+                            (step t of row i-t as row i arrives); one launch per pass, no shared
+                            memory.  k in {4, 6, 8, 10, 12} for FP32, {2, 3, 4, 6} for FP64
+                            (J2D_ERR_ARG otherwise).  Forward runs of single five-point grids
+                            only (adjoint runs take TILES, batches TILES, box plans SKEWED). */
 } j2d_algo;
 
 /* Plan options (j2d5pt_set_option / j2d5pt_get_option). */

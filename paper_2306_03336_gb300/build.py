@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libj2d5pt.so")
 LIB_CHECKED = os.path.join(HERE, "libj2d5pt_checked.so")
-UNITS = ["api.cu", "onestep.cu", "dtb.cu", "noalloc.cu"]
+UNITS = ["api.cu", "onestep.cu", "dtb.cu", "stream.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "--expt-relaxed-constexpr"]

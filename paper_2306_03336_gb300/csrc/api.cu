@@ -206,7 +206,7 @@ extern "C" j2d_status j2d5pt_set_option(j2d5pt_plan_t p, j2d_option opt, long v)
   if (!p) return fail(J2D_ERR_ARG, "set_option: null plan");
   switch (opt) {
     case J2D_OPT_ALGO:
-      if (v < J2D_ALGO_AUTO || v > J2D_ALGO_SKEWED) return fail(J2D_ERR_ARG, "set_option: bad algo %ld", v);
+      if (v < J2D_ALGO_AUTO || v > J2D_ALGO_STREAM) return fail(J2D_ERR_ARG, "set_option: bad algo %ld", v);
       p->opt_algo = (int)v;
       drop_graph(p);
       break;
@@ -303,6 +303,7 @@ static const char *algo_name(int a) {
     case J2D_ALGO_BANDS: return "bands";
     case J2D_ALGO_TILES: return "tiles";
     case J2D_ALGO_SKEWED: return "skewed";
+    case J2D_ALGO_STREAM: return "stream";
     default: return "auto";
   }
 }
@@ -359,6 +360,46 @@ static j2d_status run_grid_onestep(j2d5pt_plan_t p, int gi, const void *in, void
 static j2d_status run_dtb(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps, bool adj,
                           const DtbConfig &c, cudaStream_t s, void *states = nullptr, long state_elems = 0);
 
+// One grid, `steps` forward steps, in -> out, by the STREAM schedule: ceil(steps
+// / depth) passes between out and the plan's ping-pong buffer, the first pass
+// taking the remainder; every buffer a pass writes first receives the input's ring.
+static j2d_status run_grid_stream(j2d5pt_plan_t p, int gi, const void *in, void *out, long steps, int depth,
+                                  cudaStream_t s) {
+  const GridDesc &g = p->grids[gi];
+  if (!stream_depth_ok(p->dtype, depth))
+    return fail(J2D_ERR_ARG, "run: no stream kernel of depth %d for %s", depth, p->dtype == J2D_F64 ? "f64" : "f32");
+  const StreamGeom q = stream_geometry(p->dtype, g, depth, p->sms);
+  const long passes = (steps + q.depth - 1) / q.depth;
+  const int first = (int)(steps - (passes - 1) * q.depth);
+  void *ws = ws_of(p, gi);
+  const void *src = in;
+  cudaError_t e;
+  if (in == out && (passes & 1)) {
+    if ((e = cudaMemcpyAsync(ws, in, g.bytes(p->elem), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "run: copy");
+    src = ws;
+  }
+  if (out != in && (e = launch_ring_copy(p->dtype, in, out, g, s)) != cudaSuccess) return cuda_fail(e, "run: ring");
+  if (passes >= 2 && src != ws && (e = launch_ring_copy(p->dtype, in, ws, g, s)) != cudaSuccess)
+    return cuda_fail(e, "run: ring");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool timing = p->opt_timing && p->ev0 && cap == cudaStreamCaptureStatusNone;
+  if (timing) cudaEventRecord(p->ev0, s);
+  for (long j = 0; j < passes; ++j) {
+    void *dst = ((passes - 1 - j) % 2 == 0) ? out : ws;
+    if ((e = launch_stream_pass(p->dtype, src, dst, g, q, j == 0 ? first : q.depth, int_path_of(p), p->d_status,
+                                s)) != cudaSuccess)
+      return cuda_fail(e, "run: stream launch");
+    src = dst;
+  }
+  if (timing) {
+    cudaEventRecord(p->ev1, s);
+    p->timed = true;
+  }
+  return J2D_OK;
+}
+
 static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const *out, long steps, bool adj,
                              cudaStream_t s) {
   if (steps < 0) return fail(J2D_ERR_ARG, "run: steps %ld < 0", steps);
@@ -382,6 +423,7 @@ static j2d_status run_common(j2d5pt_plan_t p, const void *const *in, void *const
     }
     return J2D_OK;
   }
+  if (c.algo == J2D_ALGO_STREAM) return run_grid_stream(p, 0, in[0], out[0], steps, c.depth, s);
   return run_dtb(p, in, out, steps, adj, c, s);
 }
 
@@ -595,9 +637,10 @@ extern "C" j2d_status j2d5pt_run_states(j2d5pt_plan_t p, const void *in, void *s
     }
     return J2D_OK;
   }
-  if (c.algo == J2D_ALGO_SKEWED || c.sweep == 2) {
-    // the skewed and two-step sweeps hold no whole state of a strip between
-    // their steps: single-step tiles (the plan's depth and shape if it chose tiles)
+  if (c.algo == J2D_ALGO_SKEWED || c.algo == J2D_ALGO_STREAM || c.sweep == 2) {
+    // the skewed, stream and two-step sweeps hold no whole state of a strip
+    // between their steps: single-step tiles (the plan's depth and shape if it
+    // chose tiles)
     DtbRequest rq;
     rq.algo = J2D_ALGO_TILES;
     rq.depth = c.algo == J2D_ALGO_TILES ? p->opt_depth : 0;
@@ -629,7 +672,7 @@ extern "C" j2d_status j2d5pt_sync_status(j2d5pt_plan_t p) {
 
 // Autotuner.  Candidates: the one-step kernel; the resident kernel when the
 // grid fits on chip; bands, tiles and skewed tiles over temporal depths k
-// (and tile shapes).
+// (and tile shapes); the stream schedule over its steps per pass.
 // Each is timed with CUDA events for min(steps, 64) steps, or more when that
 // takes under 5 ms (best of two or three runs after a warm-up run); the
 // fastest per step is kept in the plan.  With J2D_TUNE_CACHE set, results are
@@ -715,6 +758,9 @@ static j2d_status autotune_common(j2d5pt_plan_t p, const void *const *in, void *
       for (int wx : {1, 2, 4}) cands.push_back({J2D_ALGO_TILES, d, wx});
     for (int wx : {2, 4, 8}) cands.push_back({J2D_ALGO_SKEWED, d, wx});
   }
+  if (single && !box)
+    for (int d = 1; d <= stream_max_depth(p->dtype) && d <= steps; ++d)
+      if (stream_depth_ok(p->dtype, d)) cands.push_back({J2D_ALGO_STREAM, d, 0});
   float best_ms = 1e30f;
   Cand best = {J2D_ALGO_AUTO, 0, 0};
   cudaEvent_t e0, e1;

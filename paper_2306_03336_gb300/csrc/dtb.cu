@@ -1874,6 +1874,7 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
   if (algo == J2D_ALGO_BANDS && !single) algo = J2D_ALGO_TILES;
   if (algo == J2D_ALGO_SKEWED && rq.adjoint) algo = J2D_ALGO_TILES;  // the skewed order is forward only
+  if (algo == J2D_ALGO_STREAM && (rq.adjoint || !single)) algo = J2D_ALGO_TILES;  // forward, one grid
   // the 3x3 box runs the one-step kernel or the skewed tiles
   if (grids[0].shape == 9 && algo != J2D_ALGO_ONESTEP) algo = J2D_ALGO_SKEWED;
   c.algo = algo;

@@ -72,6 +72,23 @@ cudaError_t launch_adjoint_wgrad(j2d_dtype dt, const void *u, const void *lam1, 
 // pinned host memory) to dst (row stride dpitch)
 cudaError_t launch_gather_rows(j2d_dtype dt, const void *src, long spitch, void *dst, long dpitch, long rows, long width,
                                cudaStream_t s);
+// STREAM schedule (stream.cu): temporal blocking in the register file.
+constexpr int kStreamMaxF32 = 12;  // steps per pass, at most
+constexpr int kStreamMaxF64 = 8;
+struct StreamGeom {
+  int depth = 1;  // steps per pass (M)
+  int G = 0;      // halo columns on each side of a band
+  int vw = 0;     // stored columns per band
+  int bands = 0;  // column bands
+  int H = 0;      // rows stored per run
+  int runs = 0;   // runs per band
+};
+int stream_max_depth(j2d_dtype dt);
+bool stream_depth_ok(j2d_dtype dt, int m);  // a kernel of m steps per pass exists
+StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms);
+cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const GridDesc &g, const StreamGeom &q, int m,
+                               int ipath, int *status, cudaStream_t s);
+
 cudaError_t measure_fma(j2d_dtype dt, double *rate);
 cudaError_t measure_exact(double *rate);
 cudaError_t measure_exact_box(double *rate);

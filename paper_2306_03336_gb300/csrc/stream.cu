@@ -1,0 +1,385 @@
+// stream.cu -- temporal blocking in the register file: the STREAM schedule.
+//
+// The paper's deep temporal blocking (Zhang et al., GPGPU'23, Sections 3.1 and
+// 3.3, Figure 1) keeps a tile on chip for several time steps so that one trip
+// through HBM carries many steps.  On GB300 the register file (256 KB per SM)
+// is larger than shared memory (228 KB), so this schedule keeps the time steps
+// of a tile in registers and uses no shared memory at all.
+//
+// Each warp owns one column band of the grid, 32 lanes x one 16-byte vector
+// (128 FP32 / 64 FP64 columns), and a run of rows, and sweeps the run from top
+// to bottom once per pass.  A pass advances M time steps as a pipeline: when
+// row i of the pass's input arrives, the warp evaluates step 1 of row i-1,
+// step 2 of row i-2, ..., step M of row i-M, each from the two rows of the step
+// below that it keeps in registers and the row that step has just produced
+// (the update of row r at step t reads rows r-1, r and r+1 of step t-1).  Row
+// i-M at step M leaves for HBM.  The x +- 1 neighbours come from the adjacent
+// lanes by shuffles; beyond the warp's two edges the missing neighbours spoil
+// one more column per step, so a band evaluates 32V columns and stores the
+// middle 32V - 2G (G >= M, a multiple of V): an overlapped halo in x, as the
+// paper's tiles have.  In y, a run starts M rows above its first stored row
+// and ends M rows below its last, so the runs of a band overlap by 2M rows.
+// The ring (one cell deep, held constant) is kept by holding a ring cell's
+// value at every step: ring columns in the bands that contain one (a select
+// per cell), ring rows in the few iterations of a run where a step reaches row
+// 0 or row ny+1 (a uniform test).  Cells outside the logical array never
+// reach a stored cell: the held ring separates them.
+//
+// Every cell is evaluated exactly as the one-step kernel evaluates it: FP32 by
+// the chain of stencil() in common.cuh (here two cells per paired FP32 multiply
+// and fused multiply-add, each element rounded as the scalar instruction
+// rounds it), FP64 by stencil_cell() with the integer path on the same cells.
+// So the results are bit-identical to every other kernel of the library.
+//
+// One launch per pass (the passes of a run are ordered on the stream; a run of
+// S steps is ceil(S / M) passes, the first one taking the remainder).  Per cell
+// update HBM carries 2 * sizeof(T) * (1 + overlap) / M bytes.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace j2d {
+
+constexpr int kStreamWarps = 4;  // warps per block; each warp is independent
+constexpr int kStreamThreads = 32 * kStreamWarps;
+
+struct StreamParams {
+  const void *in;
+  void *out;
+  long pitch;   // elements per row
+  int off;      // element offset of logical column 0
+  int nx, ny;
+  int G;        // halo columns on each side of a band (a multiple of V, >= the pass's steps)
+  int vw;       // stored (valid) columns per band: 32V - 2G
+  int bands;    // column bands
+  int H;        // rows stored per run
+  int runs;     // runs per band
+  int meff;     // steps of this pass (<= M: steps t > meff leave rows unchanged)
+  int ipath;    // FP64: integer path on
+  long nelem;   // elements of each buffer ((ny + 2) * pitch), for the checked build
+  int *status;  // checked build: J2D_ERR_BOUNDS is recorded here
+  double w[5];  // W, E, S, C, N
+};
+
+// ---- one lane's 16-byte vector of a row, in registers -------------------------
+
+// FP32: four columns v0..v3 held as two pairs a = (v0, v2), b = (v1, v3), so
+// that the x - 1 and x + 1 operands of each pair are pairs too (mostly the
+// other pair), and one paired instruction evaluates two cells.
+struct RowF {
+  float2 a, b;
+};
+struct WeightsF {
+  float2 w, e, s, c, n;  // each weight in both halves
+};
+
+__device__ __forceinline__ RowF row_zero(RowF *) { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+__device__ __forceinline__ RowF row_load(const float *p, RowF *) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  return {make_float2(v.x, v.z), make_float2(v.y, v.w)};
+}
+__device__ __forceinline__ void row_store(float *p, const RowF &r) {
+  *reinterpret_cast<float4 *>(p) = make_float4(r.a.x, r.b.x, r.a.y, r.b.y);
+}
+// Keep the cells whose bit is set in m (bit v: column v of the vector) at c.
+__device__ __forceinline__ RowF row_hold(RowF n, const RowF &c, unsigned m) {
+  if (m & 1u) n.a.x = c.a.x;
+  if (m & 2u) n.b.x = c.b.x;
+  if (m & 4u) n.a.y = c.a.y;
+  if (m & 8u) n.b.y = c.b.y;
+  return n;
+}
+
+// One step of the four cells of row c (ym: the row above at the same step,
+// yp: the row below), in the order of stencil(): y-1, centre, x-1, x+1, y+1.
+__device__ __forceinline__ RowF row_step(const WeightsF &k, const RowF &ym, const RowF &c, const RowF &yp) {
+  const float L = __shfl_up_sync(0xffffffffu, c.b.y, 1);    // column x0 - 1: the left lane's v3
+  const float R = __shfl_down_sync(0xffffffffu, c.a.x, 1);  // column x0 + 4: the right lane's v0
+  float2 ra = __fmul2_rn(k.s, ym.a);
+  ra = __ffma2_rn(k.c, c.a, ra);
+  ra = __ffma2_rn(k.w, make_float2(L, c.b.x), ra);  // x-1 of (v0, v2)
+  ra = __ffma2_rn(k.e, c.b, ra);                    // x+1 of (v0, v2)
+  ra = __ffma2_rn(k.n, yp.a, ra);
+  float2 rb = __fmul2_rn(k.s, ym.b);
+  rb = __ffma2_rn(k.c, c.b, rb);
+  rb = __ffma2_rn(k.w, c.a, rb);                    // x-1 of (v1, v3)
+  rb = __ffma2_rn(k.e, make_float2(c.a.y, R), rb);  // x+1 of (v1, v3)
+  rb = __ffma2_rn(k.n, yp.b, rb);
+  return {ra, rb};
+}
+
+// FP64: two columns.
+struct RowD {
+  double a, b;
+};
+struct WeightsD {
+  Links<double> l;
+  ExactW u;
+  int ipath;
+};
+
+__device__ __forceinline__ RowD row_zero(RowD *) { return {0.0, 0.0}; }
+__device__ __forceinline__ RowD row_load(const double *p, RowD *) {
+  const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void row_store(double *p, const RowD &r) {
+  *reinterpret_cast<double2 *>(p) = make_double2(r.a, r.b);
+}
+__device__ __forceinline__ RowD row_hold(RowD n, const RowD &c, unsigned m) {
+  if (m & 1u) n.a = c.a;
+  if (m & 2u) n.b = c.b;
+  return n;
+}
+// `y`: the row's logical index, which selects the integer path (the same
+// cells as in every other kernel: exact_cell()).
+__device__ __forceinline__ RowD row_step(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp, int x0,
+                                         int y) {
+  const double L = __shfl_up_sync(0xffffffffu, c.b, 1);
+  const double R = __shfl_down_sync(0xffffffffu, c.a, 1);
+  const bool ea = exact_cell(x0, y, k.ipath != 0), eb = exact_cell(x0 + 1, y, k.ipath != 0);
+  return {stencil_cell(k.l, k.u, ea, L, c.b, ym.a, c.a, yp.a), stencil_cell(k.l, k.u, eb, c.a, R, ym.b, c.b, yp.b)};
+}
+
+template <typename T> struct RowOf;
+template <> struct RowOf<float> { using R = RowF; using W = WeightsF; };
+template <> struct RowOf<double> { using R = RowD; using W = WeightsD; };
+
+__device__ __forceinline__ RowF step_any(const WeightsF &k, const RowF &ym, const RowF &c, const RowF &yp, int, int) {
+  return row_step(k, ym, c, yp);
+}
+__device__ __forceinline__ RowD step_any(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp, int x0,
+                                         int y) {
+  return row_step(k, ym, c, yp, x0, y);
+}
+
+// In the checked build, is [e, e + V) inside the buffer of nelem elements?
+__device__ __forceinline__ bool stream_ok(long e, int V, const StreamParams &p) {
+  if (!kChecked) return true;
+  const bool ok = e >= 0 && e + V <= p.nelem;
+  if (!ok) set_error(p.status, DEV_BOUNDS);
+  return ok;
+}
+
+// The pipeline of one warp: for each step t = 0..M-1 the two most recent rows
+// of step t (A: the older, B: the newer).
+template <typename T, int M, bool EDGE> struct Pipe {
+  using R = typename RowOf<T>::R;
+  using W = typename RowOf<T>::W;
+  R A[M], B[M];
+  const W &k;
+  const StreamParams &p;
+  T *out;
+  long e0;        // element offset of this lane's vector within a row
+  int x0;         // logical column of the vector's first element
+  unsigned hold;  // ring columns in this lane's vector
+  bool st;        // this lane's vector is stored
+  int y0, y1;     // stored rows [y0, y1)
+
+  __device__ __forceinline__ Pipe(const W &k_, const StreamParams &p_, T *out_, long e0_, int x0_, unsigned hold_,
+                                  bool st_, int y0_, int y1_)
+      : k(k_), p(p_), out(out_), e0(e0_), x0(x0_), hold(hold_), st(st_), y0(y0_), y1(y1_) {
+#pragma unroll
+    for (int t = 0; t < M; ++t) {
+      A[t] = row_zero((R *)nullptr);
+      B[t] = row_zero((R *)nullptr);
+    }
+  }
+
+  // Iteration i: row i of step 0 arrives; steps 1..M advance one row each.
+  // CHK: some step reaches ring row 0 or ny + 1 in this iteration, or the
+  // pass has fewer than M steps (steps beyond meff pass their rows through).
+  template <bool CHK> __device__ __forceinline__ void iter(int i, R cur) {
+#pragma unroll
+    for (int t = 1; t <= M; ++t) {
+      const int r = i - t;  // the row step t evaluates
+      R n = step_any(k, A[t - 1], B[t - 1], cur, x0, r);
+      if (EDGE) n = row_hold(n, B[t - 1], hold);
+      if (CHK && (r == 0 || r == p.ny + 1 || t > p.meff)) n = B[t - 1];
+      A[t - 1] = B[t - 1];
+      B[t - 1] = cur;
+      cur = n;
+    }
+    const int r = i - M;
+    if (st && r >= y0 && r < y1) {
+      const long e = (long)r * p.pitch + e0;
+      if (stream_ok(e, VecOf<T>::V, p)) row_store(out + e, cur);
+    }
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ typename RowOf<T>::R load_row(const T *in, const StreamParams &p, int i, long e0,
+                                                         bool live) {
+  using R = typename RowOf<T>::R;
+  if (live && i <= p.ny + 1) {
+    const long e = (long)i * p.pitch + e0;
+    if (stream_ok(e, VecOf<T>::V, p)) return row_load(in + e, (R *)nullptr);
+  }
+  return row_zero((R *)nullptr);
+}
+
+template <typename T, int M, bool EDGE>
+__device__ __forceinline__ void stream_sweep(const StreamParams &p, const typename RowOf<T>::W &k, long e0, int x0,
+                                             unsigned hold, bool live, bool st, int y0, int y1) {
+  using R = typename RowOf<T>::R;
+  const T *in = static_cast<const T *>(p.in);
+  T *out = static_cast<T *>(p.out);
+  Pipe<T, M, EDGE> pipe(k, p, out, e0, x0, hold, st, y0, y1);
+  const int a = max(y0 - M, 0);
+  const int iend = y1 + M;  // the last iteration stores row y1 - 1
+  const bool short_pass = p.meff < M;
+  // three iterations per trip: the window of each step rotates through three
+  // register sets, so the unrolled trip needs no moves; each input row is
+  // loaded three iterations before it is used
+  R q0 = load_row(in, p, a, e0, live), q1 = load_row(in, p, a + 1, e0, live), q2 = load_row(in, p, a + 2, e0, live);
+  for (int i = a; i < iend; i += 3) {
+    R c;
+    if (short_pass || i <= M || i + 2 >= p.ny + 2) {
+      c = q0; q0 = load_row(in, p, i + 3, e0, live); pipe.template iter<true>(i, c);
+      c = q1; q1 = load_row(in, p, i + 4, e0, live); pipe.template iter<true>(i + 1, c);
+      c = q2; q2 = load_row(in, p, i + 5, e0, live); pipe.template iter<true>(i + 2, c);
+    } else {
+      c = q0; q0 = load_row(in, p, i + 3, e0, live); pipe.template iter<false>(i, c);
+      c = q1; q1 = load_row(in, p, i + 4, e0, live); pipe.template iter<false>(i + 1, c);
+      c = q2; q2 = load_row(in, p, i + 5, e0, live); pipe.template iter<false>(i + 2, c);
+    }
+  }
+}
+
+__device__ __forceinline__ void make_weights(const StreamParams &p, WeightsF *k) {
+  const float w = (float)p.w[0], e = (float)p.w[1], s = (float)p.w[2], c = (float)p.w[3], n = (float)p.w[4];
+  k->w = make_float2(w, w);
+  k->e = make_float2(e, e);
+  k->s = make_float2(s, s);
+  k->c = make_float2(c, c);
+  k->n = make_float2(n, n);
+}
+__device__ __forceinline__ void make_weights(const StreamParams &p, WeightsD *k) {
+  k->l = Links<double>{p.w[0], p.w[1], p.w[2], p.w[3], p.w[4]};
+  k->u = exact_weights(k->l);
+  k->ipath = p.ipath;
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamParams p) {
+  constexpr int V = VecOf<T>::V;
+  const int lane = threadIdx.x & 31;
+  const int unit = blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
+  if (unit >= p.bands * p.runs) return;  // whole warps
+  // units in band-fastest order: the warps running at the same time cover
+  // neighbouring bands of the same rows, so the overlapped halo columns two
+  // bands read are found in L2 the second time
+  const int band = unit % p.bands, run = unit / p.bands;
+  const int xb = 1 + band * p.vw - p.G;  // logical column of lane 0's first element
+  const int x0 = xb + V * lane;
+  const long e0 = p.off + x0;
+  const bool live = e0 >= 0 && e0 + V <= p.pitch;
+  const bool st = live && x0 >= xb + p.G && x0 < xb + 32 * V - p.G && x0 <= p.nx;
+  unsigned hold = 0;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+    if (x0 + v == 0 || x0 + v == p.nx + 1) hold |= 1u << v;
+  const bool edge = __any_sync(0xffffffffu, hold != 0);
+  const int y0 = 1 + run * p.H, y1 = min(y0 + p.H, p.ny + 1);
+  typename RowOf<T>::W k;
+  make_weights(p, &k);
+  if (edge)
+    stream_sweep<T, M, true>(p, k, e0, x0, hold, live, st, y0, y1);
+  else
+    stream_sweep<T, M, false>(p, k, e0, x0, hold, live, st, y0, y1);
+}
+
+// ---- host side ------------------------------------------------------------------
+
+using StreamFn = void (*)(StreamParams);
+
+template <typename T, int... Ms> struct StreamTable;
+template <typename T> struct StreamTable<T> {
+  static StreamFn get(int) { return nullptr; }
+};
+template <typename T, int M0, int... Ms> struct StreamTable<T, M0, Ms...> {
+  static StreamFn get(int m) { return m == M0 ? stream_kernel<T, M0> : StreamTable<T, Ms...>::get(m); }
+};
+
+int stream_max_depth(j2d_dtype dt) { return dt == J2D_F64 ? kStreamMaxF64 : kStreamMaxF32; }
+
+// Steps per pass with a kernel of their own; a run's shorter pass runs the
+// kernel of the run's depth with fewer steps.
+static StreamFn stream_fn(j2d_dtype dt, int m) {
+  if (dt == J2D_F64) return StreamTable<double, 2, 3, 4, 6>::get(m);
+  return StreamTable<float, 4, 6, 8, 10, 12>::get(m);
+}
+
+bool stream_depth_ok(j2d_dtype dt, int m) { return stream_fn(dt, m) != nullptr; }
+
+// Resident blocks per SM of one instantiation (cached).
+static int stream_occupancy(j2d_dtype dt, int m) {
+  static std::mutex mu;
+  static int cache[2][16] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  int &c = cache[dt == J2D_F64 ? 1 : 0][m];
+  if (c == 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_fn(dt, m), kStreamThreads, 0) != cudaSuccess ||
+        nb < 1) {
+      cudaGetLastError();
+      nb = 1;
+    }
+    c = nb;
+  }
+  return c;
+}
+
+StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) {
+  StreamGeom q;
+  const int V = dt == J2D_F64 ? 2 : 4;
+  q.depth = std::max(1, std::min(depth, stream_max_depth(dt)));
+  q.G = (q.depth + V - 1) / V * V;
+  q.vw = 32 * V - 2 * q.G;
+  q.bands = (g.nx + q.vw - 1) / q.vw;
+  // one wave of units: as many runs per band as the resident warps allow,
+  // each run at least 4M rows tall (its 2M-row overlap then costs <= 50%)
+  const long warps = (long)stream_occupancy(dt, q.depth) * kStreamWarps * std::max(sms, 1);
+  const int hmin = 4 * q.depth;
+  int runs = (int)std::max<long>(1, warps / q.bands);
+  runs = std::min(runs, std::max(1, g.ny / hmin));
+  q.H = (g.ny + runs - 1) / runs;
+  q.runs = (g.ny + q.H - 1) / q.H;
+  return q;
+}
+
+// A pass of m <= q.depth steps, in -> out (distinct buffers whose rings agree).
+cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const GridDesc &g, const StreamGeom &q, int m,
+                               int ipath, int *status, cudaStream_t s) {
+  StreamParams p;
+  p.in = in;
+  p.out = out;
+  p.pitch = g.pitch;
+  p.off = (int)g.off;
+  p.nx = g.nx;
+  p.ny = g.ny;
+  p.G = q.G;
+  p.vw = q.vw;
+  p.bands = q.bands;
+  p.H = q.H;
+  p.runs = q.runs;
+  p.meff = m;
+  p.ipath = ipath;
+  p.nelem = (long)(g.ny + 2) * g.pitch;
+  p.status = status;
+  for (int i = 0; i < 5; ++i) p.w[i] = g.w[i];
+  StreamFn fn = stream_fn(dt, q.depth);
+  if (!fn || m < 1 || m > q.depth) return cudaErrorInvalidValue;
+  const long units = (long)q.bands * q.runs;
+  const unsigned blocks = (unsigned)((units + kStreamWarps - 1) / kStreamWarps);
+  fn<<<blocks, kStreamThreads, 0, s>>>(p);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace j2d

@@ -22,7 +22,7 @@ LIB_CHECKED_PATH = os.path.join(_HERE, "libj2d5pt_checked.so")
 J2D_F64, J2D_F32 = 0, 1
 J2D_OK, J2D_ERR_ARG, J2D_ERR_ALIGN, J2D_ERR_NOMEM, J2D_ERR_DEVICE = 0, 1, 2, 3, 4
 J2D_ERR_UNSUPPORTED, J2D_ERR_TIMEOUT, J2D_ERR_BOUNDS = 5, 6, 7
-ALGO = {"auto": 0, "onestep": 1, "resident": 2, "bands": 3, "tiles": 4, "skewed": 5}
+ALGO = {"auto": 0, "onestep": 1, "resident": 2, "bands": 3, "tiles": 4, "skewed": 5, "stream": 6}
 OPT = {"algo": 0, "depth": 1, "tile_wx": 2, "ctas": 3, "timeout_ms": 4, "verbose": 5, "graph": 6, "timing": 7, "fault_inject": 8,
        "int_path": 9, "sweep_steps": 10}
 STATUS_NAMES = {0: "J2D_OK", 1: "J2D_ERR_ARG", 2: "J2D_ERR_ALIGN", 3: "J2D_ERR_NOMEM", 4: "J2D_ERR_DEVICE",

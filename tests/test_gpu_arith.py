@@ -94,7 +94,7 @@ def _weights():
 
 
 NX, NY = 70, 45
-ALGOS = ["onestep", "resident", "bands", "tiles", "skewed"]
+ALGOS = ["onestep", "resident", "bands", "tiles", "skewed", "stream"]
 
 
 @pytest.fixture(scope="module")

@@ -53,7 +53,7 @@ def _run_checked(lib, u0, w, steps, algo, depth, wx, adjoint=False, box=False):
 
 SIZES = [(1, 1), (1, 7), (7, 1), (13, 17), (127, 131), (257, 300), (509, 3)]
 FAMILIES = [("onestep", 0, 0), ("resident", 0, 0), ("bands", 3, 0), ("tiles", 3, 2), ("tiles", 5, 16), ("skewed", 3, 4),
-            ("skewed", 6, 1)]
+            ("skewed", 6, 1), ("stream", 3, 0), ("stream", 6, 0)]
 
 
 @pytest.mark.parametrize("algo,depth,wx", FAMILIES)

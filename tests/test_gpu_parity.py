@@ -15,7 +15,7 @@ from tests.gpu_util import TOL_F64, cell_rel_err, f32_bound, rel_err
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = ["onestep", "resident", "bands", "tiles", "skewed"]
+ALGOS = ["onestep", "resident", "bands", "tiles", "skewed", "stream"]
 DEPTH = {"bands": 3, "tiles": 3, "skewed": 3}
 
 
