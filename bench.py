@@ -228,6 +228,35 @@ def roof_f32_dtb(pk, kernel_gcells, sweep):
             "kernel_gcells": round(kernel_gcells, 3)}
 
 
+def roof_f32_stream(pk, kernel_gcells, depth):
+    """FP32 stream schedule (temporal blocking in registers): no shared-memory
+    sweep; each cell update is 5 FMA-pipe operations (paired two to an
+    instruction), so the bound is the FP32 pipe.  HBM carries one read and
+    one write of the grid per pass of `depth` steps, plus the bands'
+    overlapped x halo (128 columns read per 128 - 2G stored, G = depth
+    rounded up to a whole vector): reported beside it."""
+    g = (depth + 3) // 4 * 4
+    bpc = 4.0 * (128.0 / (128 - 2 * g) + 1.0) / depth
+    achieved = kernel_gcells * 9 / 1e3
+    peak = pk["fma32"] / 5 * 9 / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "kernel": "stream_kernel",
+            "hbm_bytes_per_cell_update": round(bpc, 4),
+            "frac_hbm": round(kernel_gcells * bpc / (pk["hbm"] / 1e9), 4) if pk["hbm"] else None,
+            "peak_source": "of measured: FP32 FMA j2d5pt_measure_fma_rate / 5 per cell; x 9 flops per cell",
+            "kernel_gcells": round(kernel_gcells, 3), "peak_gcells": round(pk["fma32"] / 5 / 1e9, 2)}
+
+
+def roof_f32(pk, kernel_gcells, desc):
+    """The FP32 roofline record of whichever blocked schedule a plan runs."""
+    f = dict(kv.split("=") for kv in desc.split())
+    if f["algo"] == "stream":
+        return roof_f32_stream(pk, kernel_gcells, int(f["depth"]))
+    if f["algo"] == "onestep":
+        return roof_hbm(pk, kernel_gcells, 4)
+    return roof_f32_dtb(pk, kernel_gcells, int(f.get("sweep", "1")))
+
+
 def roof_hbm(pk, kernel_gcells, elem):
     """One-step kernel, HBM: one read and one write of the element per cell update."""
     if not pk["hbm"]:
@@ -448,8 +477,7 @@ def run_extras(j2d5pt, synth, flush, stream, pk, head_plan, head_src, head_dst):
     p.autotune(a, b, T)
     p.set("timing", 1)
     r2 = reps(p, lambda: p.run(a, b, T, stream), flush, stream, cells)
-    sweep = int(dict(kv.split("=") for kv in p.describe().split()).get("sweep", "1"))
-    r2["roofline"] = roof_f32_dtb(pk, r2["kernel_gcells"], sweep)
+    r2["roofline"] = roof_f32(pk, r2["kernel_gcells"], p.describe())
     r2["plan"] = p.describe()
     err, how = oracle_blocks_err(u0.astype(np.float32).astype(np.float64), w, T, p.view(b))
     out["f32_16384x16384_1000"] = {"onestep": r1, "autotuned": r2, "max_rel_err_vs_fp64_oracle": err,
@@ -474,8 +502,7 @@ def run_extras(j2d5pt, synth, flush, stream, pk, head_plan, head_src, head_dst):
         if dt == "f64":
             r["roofline"] = roof_f64(pk, r["kernel_gcells"])
         else:
-            sw = int(dict(kv.split("=") for kv in p.describe().split()).get("sweep", "1"))
-            r["roofline"] = roof_f32_dtb(pk, r["kernel_gcells"], sw)
+            r["roofline"] = roof_f32(pk, r["kernel_gcells"], p.describe())
         r["plan"] = p.describe()
         pd[dt] = r
         p.close()
@@ -636,6 +663,8 @@ WORKLOADS = {
     "f32tiles": (8192, 8192, "f32", "tiles", 16, 2, 16, 1),
     "f32skewed": (8192, 8192, "f32", "skewed", 16, 8, 32, 1),
     "f32onestep": (8192, 8192, "f32", "onestep", 0, 0, 4, 1),
+    "f32stream": (8192, 8192, "f32", "stream", 8, 0, 16, 1),
+    "f64stream": (8192, 8192, "f64", "stream", 2, 0, 4, 1),
     "f64box": (8192, 8192, "f64", "box:skewed", 4, 4, 8, 1),
     "f64batch": (64, 0, "f64", "batch:resident", 0, 0, 20, 1),
 }

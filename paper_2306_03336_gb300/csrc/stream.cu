@@ -44,8 +44,12 @@
 
 namespace j2d {
 
-constexpr int kStreamWarps = 4;  // warps per block; each warp is independent
-constexpr int kStreamThreads = 32 * kStreamWarps;
+// Warps per block (each warp is independent): FP32 one, so that registers
+// are granted warp by warp (FP32 16384^2, k = 8: 3808 against 3228 GCells/s
+// with four-warp blocks); FP64 four (155.6 against 161.2 with one).
+template <typename T> struct WarpsOf { static constexpr int W = 1; };
+template <> struct WarpsOf<double> { static constexpr int W = 4; };
+inline int stream_warps(j2d_dtype dt) { return dt == J2D_F64 ? WarpsOf<double>::W : WarpsOf<float>::W; }
 
 struct StreamParams {
   const void *in;
@@ -96,18 +100,23 @@ __device__ __forceinline__ RowF row_hold(RowF n, const RowF &c, unsigned m) {
 
 // One step of the four cells of row c (ym: the row above at the same step,
 // yp: the row below), in the order of stencil(): y-1, centre, x-1, x+1, y+1.
+// The two operand pairs that would mix registers of both pairs (x-1 of
+// (v0, v2) is (L, v1); x+1 of (v1, v3) is (v2, R)) take two scalar FMAs each
+// instead of a move into a register pair and one paired FMA.
 __device__ __forceinline__ RowF row_step(const WeightsF &k, const RowF &ym, const RowF &c, const RowF &yp) {
   const float L = __shfl_up_sync(0xffffffffu, c.b.y, 1);    // column x0 - 1: the left lane's v3
   const float R = __shfl_down_sync(0xffffffffu, c.a.x, 1);  // column x0 + 4: the right lane's v0
   float2 ra = __fmul2_rn(k.s, ym.a);
   ra = __ffma2_rn(k.c, c.a, ra);
-  ra = __ffma2_rn(k.w, make_float2(L, c.b.x), ra);  // x-1 of (v0, v2)
-  ra = __ffma2_rn(k.e, c.b, ra);                    // x+1 of (v0, v2)
+  ra.x = __fmaf_rn(k.w.x, L, ra.x);      // x-1 of v0
+  ra.y = __fmaf_rn(k.w.x, c.b.x, ra.y);  // x-1 of v2
+  ra = __ffma2_rn(k.e, c.b, ra);         // x+1 of (v0, v2)
   ra = __ffma2_rn(k.n, yp.a, ra);
   float2 rb = __fmul2_rn(k.s, ym.b);
   rb = __ffma2_rn(k.c, c.b, rb);
-  rb = __ffma2_rn(k.w, c.a, rb);                    // x-1 of (v1, v3)
-  rb = __ffma2_rn(k.e, make_float2(c.a.y, R), rb);  // x+1 of (v1, v3)
+  rb = __ffma2_rn(k.w, c.a, rb);         // x-1 of (v1, v3)
+  rb.x = __fmaf_rn(k.e.x, c.a.y, rb.x);  // x+1 of v1
+  rb.y = __fmaf_rn(k.e.x, R, rb.y);      // x+1 of v3
   rb = __ffma2_rn(k.n, yp.b, rb);
   return {ra, rb};
 }
@@ -119,7 +128,6 @@ struct RowD {
 struct WeightsD {
   Links<double> l;
   ExactW u;
-  int ipath;
 };
 
 __device__ __forceinline__ RowD row_zero(RowD *) { return {0.0, 0.0}; }
@@ -135,26 +143,28 @@ __device__ __forceinline__ RowD row_hold(RowD n, const RowD &c, unsigned m) {
   if (m & 2u) n.b = c.b;
   return n;
 }
-// `y`: the row's logical index, which selects the integer path (the same
-// cells as in every other kernel: exact_cell()).
-__device__ __forceinline__ RowD row_step(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp, int x0,
-                                         int y) {
+// `exact`: the row's cells take the integer path (exact_cell() of the row:
+// the same cells as in every other kernel).
+__device__ __forceinline__ RowD row_step(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp,
+                                         bool exact) {
   const double L = __shfl_up_sync(0xffffffffu, c.b, 1);
   const double R = __shfl_down_sync(0xffffffffu, c.a, 1);
-  const bool ea = exact_cell(x0, y, k.ipath != 0), eb = exact_cell(x0 + 1, y, k.ipath != 0);
-  return {stencil_cell(k.l, k.u, ea, L, c.b, ym.a, c.a, yp.a), stencil_cell(k.l, k.u, eb, c.a, R, ym.b, c.b, yp.b)};
+  return {stencil_cell(k.l, k.u, exact, L, c.b, ym.a, c.a, yp.a),
+          stencil_cell(k.l, k.u, exact, c.a, R, ym.b, c.b, yp.b)};
 }
 
 template <typename T> struct RowOf;
 template <> struct RowOf<float> { using R = RowF; using W = WeightsF; };
 template <> struct RowOf<double> { using R = RowD; using W = WeightsD; };
 
-__device__ __forceinline__ RowF step_any(const WeightsF &k, const RowF &ym, const RowF &c, const RowF &yp, int, int) {
+// `exact`: the row takes the integer path (FP64; known at compile time where
+// the trip's row phases are).
+__device__ __forceinline__ RowF step_any(const WeightsF &k, const RowF &ym, const RowF &c, const RowF &yp, bool) {
   return row_step(k, ym, c, yp);
 }
-__device__ __forceinline__ RowD step_any(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp, int x0,
-                                         int y) {
-  return row_step(k, ym, c, yp, x0, y);
+__device__ __forceinline__ RowD step_any(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp,
+                                         bool exact) {
+  return row_step(k, ym, c, yp, exact);
 }
 
 // In the checked build, is [e, e + V) inside the buffer of nelem elements?
@@ -165,9 +175,13 @@ __device__ __forceinline__ bool stream_ok(long e, int V, const StreamParams &p) 
   return ok;
 }
 
+// The integer-path pattern must not depend on the column: one flag serves
+// both cells of a lane's vector.
+static_assert(((kExactMask >> 1) & 0x55u) == (kExactMask & 0x55u), "integer-path cells differ within a row");
+
 // The pipeline of one warp: for each step t = 0..M-1 the two most recent rows
 // of step t (A: the older, B: the newer).
-template <typename T, int M, bool EDGE> struct Pipe {
+template <typename T, int M, bool EDGE, bool IP> struct Pipe {
   using R = typename RowOf<T>::R;
   using W = typename RowOf<T>::W;
   R A[M], B[M];
@@ -193,11 +207,15 @@ template <typename T, int M, bool EDGE> struct Pipe {
   // Iteration i: row i of step 0 arrives; steps 1..M advance one row each.
   // CHK: some step reaches ring row 0 or ny + 1 in this iteration, or the
   // pass has fewer than M steps (steps beyond meff pass their rows through).
-  template <bool CHK> __device__ __forceinline__ void iter(int i, R cur) {
+  // ph: i mod 4 when the caller knows it at compile time (FP64 trips), so
+  // that each step's integer-path choice (exact_cell(): rows y mod 4 in
+  // {0, 1}) is a constant; -1 otherwise.
+  template <bool CHK> __device__ __forceinline__ void iter(int i, R cur, int ph) {
 #pragma unroll
     for (int t = 1; t <= M; ++t) {
       const int r = i - t;  // the row step t evaluates
-      R n = step_any(k, A[t - 1], B[t - 1], cur, x0, r);
+      const bool exact = IP && exact_cell(x0, ph >= 0 ? ph - t + 4 * M : r, true);
+      R n = step_any(k, A[t - 1], B[t - 1], cur, exact);
       if (EDGE) n = row_hold(n, B[t - 1], hold);
       if (CHK && (r == 0 || r == p.ny + 1 || t > p.meff)) n = B[t - 1];
       A[t - 1] = B[t - 1];
@@ -212,43 +230,92 @@ template <typename T, int M, bool EDGE> struct Pipe {
   }
 };
 
+// Input rows reach the warp through a ring of shared-memory slots of one row
+// each (16 bytes per lane), filled by asynchronous copies kAhead rows ahead of
+// use: the copies wait in the memory system instead of in registers.  Each
+// lane copies and reads back only its own 16 bytes, so the ring needs no
+// synchronisation beyond the lane's own copy groups.  The ring has two trips'
+// worth of slots (2U >= kAhead + 2), so a slot is refilled at least two
+// iterations after it was read.
+constexpr int kAhead = 4;
+
+// Iterations per trip of the sweep loop.  FP32: 3, the period of a step's
+// three-row window, so the unrolled trip rotates its registers without moves.
+// FP64: 4, the period of the integer-path row pattern (trips start on rows 0
+// mod 4, so each step's choice between the integer path and the FMA chain is
+// known at compile time and the trip is straight-line code).
+template <typename T> struct TripOf { static constexpr int U = 3; };
+template <> struct TripOf<double> { static constexpr int U = 4; };
+constexpr int kStageMax = 8;  // slots per warp, the largest 2U
+
+__device__ __forceinline__ void stage_copy(uint32_t dst, const void *src, bool on) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(on ? 16 : 0) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 1) : "memory"); }
+__device__ __forceinline__ void stage_drain() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Start the copy of input row i into the slot at shared address dst (rows
+// past the ring row ny + 1, and vectors outside the row, read as zero).
 template <typename T>
-__device__ __forceinline__ typename RowOf<T>::R load_row(const T *in, const StreamParams &p, int i, long e0,
-                                                         bool live) {
-  using R = typename RowOf<T>::R;
-  if (live && i <= p.ny + 1) {
-    const long e = (long)i * p.pitch + e0;
-    if (stream_ok(e, VecOf<T>::V, p)) return row_load(in + e, (R *)nullptr);
-  }
-  return row_zero((R *)nullptr);
+__device__ __forceinline__ void issue_row(const T *in, const StreamParams &p, int i, long e0, bool live, uint32_t dst) {
+  bool on = live && i <= p.ny + 1;
+  const long e = on ? (long)i * p.pitch + e0 : 0;
+  if (on) on = stream_ok(e, VecOf<T>::V, p);
+  stage_copy(dst, in + (on ? e : 0), on);
 }
 
-template <typename T, int M, bool EDGE>
+__device__ __forceinline__ RowF read_slot(const float4 *q, RowF *) {
+  const float4 v = *q;
+  return {make_float2(v.x, v.z), make_float2(v.y, v.w)};
+}
+__device__ __forceinline__ RowD read_slot(const float4 *q, RowD *) {
+  const double2 v = *reinterpret_cast<const double2 *>(q);
+  return {v.x, v.y};
+}
+
+template <typename T, int M, bool EDGE, bool IP>
 __device__ __forceinline__ void stream_sweep(const StreamParams &p, const typename RowOf<T>::W &k, long e0, int x0,
-                                             unsigned hold, bool live, bool st, int y0, int y1) {
+                                             unsigned hold, bool live, bool st, int y0, int y1, float4 *ring) {
   using R = typename RowOf<T>::R;
+  constexpr int U = TripOf<T>::U;
+  constexpr int S = 2 * U;  // slots
+  static_assert(S >= kAhead + 2 && S <= kStageMax, "ring too small");
   const T *in = static_cast<const T *>(p.in);
   T *out = static_cast<T *>(p.out);
-  Pipe<T, M, EDGE> pipe(k, p, out, e0, x0, hold, st, y0, y1);
-  const int a = max(y0 - M, 0);
+  Pipe<T, M, EDGE, IP> pipe(k, p, out, e0, x0, hold, st, y0, y1);
+  int a = max(y0 - M, 0);  // earlier rows only warm the pipeline up
+  if (U == 4) a &= ~3;
   const int iend = y1 + M;  // the last iteration stores row y1 - 1
   const bool short_pass = p.meff < M;
-  // three iterations per trip: the window of each step rotates through three
-  // register sets, so the unrolled trip needs no moves; each input row is
-  // loaded three iterations before it is used
-  R q0 = load_row(in, p, a, e0, live), q1 = load_row(in, p, a + 1, e0, live), q2 = load_row(in, p, a + 2, e0, live);
-  for (int i = a; i < iend; i += 3) {
-    R c;
-    if (short_pass || i <= M || i + 2 >= p.ny + 2) {
-      c = q0; q0 = load_row(in, p, i + 3, e0, live); pipe.template iter<true>(i, c);
-      c = q1; q1 = load_row(in, p, i + 4, e0, live); pipe.template iter<true>(i + 1, c);
-      c = q2; q2 = load_row(in, p, i + 5, e0, live); pipe.template iter<true>(i + 2, c);
+  // this lane's slot j is ring[32 * j]; row a + n sits in slot n mod S
+  const uint32_t base = smem_u32(ring);
+#pragma unroll
+  for (int j = 0; j < kAhead; ++j) issue_row(in, p, a + j, e0, live, base + 512u * j);
+  int s = 0;  // slot of row i: 0 or U
+  for (int i = a; i < iend; i += U) {
+    if (short_pass || i <= M || i + U - 1 >= p.ny + 2) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        stage_wait();
+        const R c = read_slot(ring + 32 * (s + u), (R *)nullptr);
+        const int sn = s + u + kAhead;
+        issue_row(in, p, i + u + kAhead, e0, live, base + 512u * (sn >= S ? sn - S : sn));
+        pipe.template iter<true>(i + u, c, U == 4 ? u : -1);
+      }
     } else {
-      c = q0; q0 = load_row(in, p, i + 3, e0, live); pipe.template iter<false>(i, c);
-      c = q1; q1 = load_row(in, p, i + 4, e0, live); pipe.template iter<false>(i + 1, c);
-      c = q2; q2 = load_row(in, p, i + 5, e0, live); pipe.template iter<false>(i + 2, c);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        stage_wait();
+        const R c = read_slot(ring + 32 * (s + u), (R *)nullptr);
+        const int sn = s + u + kAhead;
+        issue_row(in, p, i + u + kAhead, e0, live, base + 512u * (sn >= S ? sn - S : sn));
+        pipe.template iter<false>(i + u, c, U == 4 ? u : -1);
+      }
     }
+    s = s == 0 ? U : 0;
   }
+  stage_drain();
 }
 
 __device__ __forceinline__ void make_weights(const StreamParams &p, WeightsF *k) {
@@ -262,14 +329,13 @@ __device__ __forceinline__ void make_weights(const StreamParams &p, WeightsF *k)
 __device__ __forceinline__ void make_weights(const StreamParams &p, WeightsD *k) {
   k->l = Links<double>{p.w[0], p.w[1], p.w[2], p.w[3], p.w[4]};
   k->u = exact_weights(k->l);
-  k->ipath = p.ipath;
 }
 
-template <typename T, int M>
-__global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamParams p) {
+template <typename T, int M, bool IP>
+__global__ void __launch_bounds__(32 * WarpsOf<T>::W) stream_kernel(StreamParams p) {
   constexpr int V = VecOf<T>::V;
   const int lane = threadIdx.x & 31;
-  const int unit = blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
+  const int unit = blockIdx.x * WarpsOf<T>::W + (threadIdx.x >> 5);
   if (unit >= p.bands * p.runs) return;  // whole warps
   // units in band-fastest order: the warps running at the same time cover
   // neighbouring bands of the same rows, so the overlapped halo columns two
@@ -288,34 +354,37 @@ __global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamParams p) 
   const int y0 = 1 + run * p.H, y1 = min(y0 + p.H, p.ny + 1);
   typename RowOf<T>::W k;
   make_weights(p, &k);
+  __shared__ float4 ring[WarpsOf<T>::W][2 * TripOf<T>::U * 32];
+  float4 *mine = &ring[threadIdx.x >> 5][lane];
   if (edge)
-    stream_sweep<T, M, true>(p, k, e0, x0, hold, live, st, y0, y1);
+    stream_sweep<T, M, true, IP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
   else
-    stream_sweep<T, M, false>(p, k, e0, x0, hold, live, st, y0, y1);
+    stream_sweep<T, M, false, IP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
 }
 
 // ---- host side ------------------------------------------------------------------
 
 using StreamFn = void (*)(StreamParams);
 
-template <typename T, int... Ms> struct StreamTable;
-template <typename T> struct StreamTable<T> {
+template <typename T, bool IP, int... Ms> struct StreamTable;
+template <typename T, bool IP> struct StreamTable<T, IP> {
   static StreamFn get(int) { return nullptr; }
 };
-template <typename T, int M0, int... Ms> struct StreamTable<T, M0, Ms...> {
-  static StreamFn get(int m) { return m == M0 ? stream_kernel<T, M0> : StreamTable<T, Ms...>::get(m); }
+template <typename T, bool IP, int M0, int... Ms> struct StreamTable<T, IP, M0, Ms...> {
+  static StreamFn get(int m) { return m == M0 ? stream_kernel<T, M0, IP> : StreamTable<T, IP, Ms...>::get(m); }
 };
 
 int stream_max_depth(j2d_dtype dt) { return dt == J2D_F64 ? kStreamMaxF64 : kStreamMaxF32; }
 
 // Steps per pass with a kernel of their own; a run's shorter pass runs the
 // kernel of the run's depth with fewer steps.
-static StreamFn stream_fn(j2d_dtype dt, int m) {
-  if (dt == J2D_F64) return StreamTable<double, 2, 3, 4, 6>::get(m);
-  return StreamTable<float, 4, 6, 8, 10, 12>::get(m);
+static StreamFn stream_fn(j2d_dtype dt, int m, int ipath) {
+  if (dt == J2D_F64)
+    return ipath ? StreamTable<double, true, 2, 3, 4, 6>::get(m) : StreamTable<double, false, 2, 3, 4, 6>::get(m);
+  return StreamTable<float, false, 4, 6, 8, 10, 12>::get(m);
 }
 
-bool stream_depth_ok(j2d_dtype dt, int m) { return stream_fn(dt, m) != nullptr; }
+bool stream_depth_ok(j2d_dtype dt, int m) { return stream_fn(dt, m, 1) != nullptr; }
 
 // Resident blocks per SM of one instantiation (cached).
 static int stream_occupancy(j2d_dtype dt, int m) {
@@ -325,7 +394,7 @@ static int stream_occupancy(j2d_dtype dt, int m) {
   int &c = cache[dt == J2D_F64 ? 1 : 0][m];
   if (c == 0) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_fn(dt, m), kStreamThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_fn(dt, m, 1), 32 * stream_warps(dt), 0) != cudaSuccess ||
         nb < 1) {
       cudaGetLastError();
       nb = 1;
@@ -344,7 +413,7 @@ StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) 
   q.bands = (g.nx + q.vw - 1) / q.vw;
   // one wave of units: as many runs per band as the resident warps allow,
   // each run at least 4M rows tall (its 2M-row overlap then costs <= 50%)
-  const long warps = (long)stream_occupancy(dt, q.depth) * kStreamWarps * std::max(sms, 1);
+  const long warps = (long)stream_occupancy(dt, q.depth) * stream_warps(dt) * std::max(sms, 1);
   const int hmin = 4 * q.depth;
   int runs = (int)std::max<long>(1, warps / q.bands);
   runs = std::min(runs, std::max(1, g.ny / hmin));
@@ -373,11 +442,12 @@ cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const Gr
   p.nelem = (long)(g.ny + 2) * g.pitch;
   p.status = status;
   for (int i = 0; i < 5; ++i) p.w[i] = g.w[i];
-  StreamFn fn = stream_fn(dt, q.depth);
+  StreamFn fn = stream_fn(dt, q.depth, ipath);
   if (!fn || m < 1 || m > q.depth) return cudaErrorInvalidValue;
   const long units = (long)q.bands * q.runs;
-  const unsigned blocks = (unsigned)((units + kStreamWarps - 1) / kStreamWarps);
-  fn<<<blocks, kStreamThreads, 0, s>>>(p);
+  const int W = stream_warps(dt);
+  const unsigned blocks = (unsigned)((units + W - 1) / W);
+  fn<<<blocks, 32 * W, 0, s>>>(p);
   note_launch();
   return cudaGetLastError();
 }
