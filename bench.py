@@ -132,6 +132,11 @@ def traffic_for(key):
     return ent.get("bytes_per_launch")
 
 
+def kernel_of(algo):
+    """The stencil kernel a plan's algorithm launches."""
+    return {"onestep": "onestep_kernel", "stream": "stream_kernel"}.get(algo, "dtb_kernel")
+
+
 def algo_of(plan):
     return plan.describe().split("algo=")[1].split()[0]
 
@@ -322,8 +327,7 @@ def run_ours(args):
 
     pk = measure_peaks(j2d5pt)
     kern_ms = statistics.mean(kern)
-    roof = roof_f64(pk, gcells(cells, kern_ms), traffic_for("f64_16384x16384_1000_" + algo),
-                    "dtb_kernel" if algo != "onestep" else "onestep_kernel")
+    roof = roof_f64(pk, gcells(cells, kern_ms), traffic_for("f64_16384x16384_1000_" + algo), kernel_of(algo))
 
     # end to end through the C ABI on host buffers (pinned input and output)
     host_in = torch.from_numpy(u0).pin_memory().numpy()
@@ -437,7 +441,7 @@ def run_extras(j2d5pt, synth, flush, stream, pk, head_plan, head_src, head_dst):
     pa.autotune(a, b, T)
     pa.set("timing", 1)
     r = reps(pa, lambda: pa.run(a, b, T, stream), flush, stream, cells)
-    r["roofline"] = roof_f64(pk, r["kernel_gcells"])
+    r["roofline"] = roof_f64(pk, r["kernel_gcells"], kernel=kernel_of(algo_of(pa)))
     r["plan"] = pa.describe()
     fam["autotuned"] = r
     pa.close()
@@ -500,7 +504,7 @@ def run_extras(j2d5pt, synth, flush, stream, pk, head_plan, head_src, head_dst):
         r = reps(p, lambda: p.run(a, b, 1000, stream), flush, stream, nx_ * ny_ * 1000)
         r["gcells_valid_8192sq"] = round(r["gcells"] * 8192 * 8192 / (nx_ * ny_), 2)
         if dt == "f64":
-            r["roofline"] = roof_f64(pk, r["kernel_gcells"])
+            r["roofline"] = roof_f64(pk, r["kernel_gcells"], kernel=kernel_of(algo_of(p)))
         else:
             r["roofline"] = roof_f32(pk, r["kernel_gcells"], p.describe())
         r["plan"] = p.describe()
