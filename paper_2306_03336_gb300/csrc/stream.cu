@@ -143,28 +143,29 @@ __device__ __forceinline__ RowD row_hold(RowD n, const RowD &c, unsigned m) {
   if (m & 2u) n.b = c.b;
   return n;
 }
-// `exact`: the row's cells take the integer path (exact_cell() of the row:
-// the same cells as in every other kernel).
+// ea, eb: the row's two cells take the integer path (exact_cell(): the same
+// cells as in every other kernel).
 __device__ __forceinline__ RowD row_step(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp,
-                                         bool exact) {
+                                         bool ea, bool eb) {
   const double L = __shfl_up_sync(0xffffffffu, c.b, 1);
   const double R = __shfl_down_sync(0xffffffffu, c.a, 1);
-  return {stencil_cell(k.l, k.u, exact, L, c.b, ym.a, c.a, yp.a),
-          stencil_cell(k.l, k.u, exact, c.a, R, ym.b, c.b, yp.b)};
+  return {stencil_cell(k.l, k.u, ea, L, c.b, ym.a, c.a, yp.a), stencil_cell(k.l, k.u, eb, c.a, R, ym.b, c.b, yp.b)};
 }
 
 template <typename T> struct RowOf;
 template <> struct RowOf<float> { using R = RowF; using W = WeightsF; };
 template <> struct RowOf<double> { using R = RowD; using W = WeightsD; };
 
-// `exact`: the row takes the integer path (FP64; known at compile time where
-// the trip's row phases are).
-__device__ __forceinline__ RowF step_any(const WeightsF &k, const RowF &ym, const RowF &c, const RowF &yp, bool) {
+// ea, eb: the lane's first / second cell takes the integer path (FP64; known
+// at compile time where the trip's row phases are: the column parities of a
+// lane's two cells are fixed, its first column being odd).
+__device__ __forceinline__ RowF step_any(const WeightsF &k, const RowF &ym, const RowF &c, const RowF &yp, bool,
+                                         bool) {
   return row_step(k, ym, c, yp);
 }
-__device__ __forceinline__ RowD step_any(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp,
-                                         bool exact) {
-  return row_step(k, ym, c, yp, exact);
+__device__ __forceinline__ RowD step_any(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp, bool ea,
+                                         bool eb) {
+  return row_step(k, ym, c, yp, ea, eb);
 }
 
 // In the checked build, is [e, e + V) inside the buffer of nelem elements?
@@ -174,10 +175,6 @@ __device__ __forceinline__ bool stream_ok(long e, int V, const StreamParams &p) 
   if (!ok) set_error(p.status, DEV_BOUNDS);
   return ok;
 }
-
-// The integer-path pattern must not depend on the column: one flag serves
-// both cells of a lane's vector.
-static_assert(((kExactMask >> 1) & 0x55u) == (kExactMask & 0x55u), "integer-path cells differ within a row");
 
 // The pipeline of one warp: for each step t = 0..M-1 the two most recent rows
 // of step t (A: the older, B: the newer).
@@ -214,8 +211,8 @@ template <typename T, int M, bool EDGE, bool IP> struct Pipe {
 #pragma unroll
     for (int t = 1; t <= M; ++t) {
       const int r = i - t;  // the row step t evaluates
-      const bool exact = IP && exact_cell(x0, ph >= 0 ? ph - t + 4 * M : r, true);
-      R n = step_any(k, A[t - 1], B[t - 1], cur, exact);
+      const int yy = ph >= 0 ? ph - t + 4 * M : r;  // the row, or a row of the same phase mod 4
+      R n = step_any(k, A[t - 1], B[t - 1], cur, IP && exact_cell(1, yy, true), IP && exact_cell(0, yy, true));
       if (EDGE) n = row_hold(n, B[t - 1], hold);
       if (CHK && (r == 0 || r == p.ny + 1 || t > p.meff)) n = B[t - 1];
       A[t - 1] = B[t - 1];
