@@ -78,8 +78,9 @@ typedef enum {
                             rows, advancing k steps per pass as a pipeline held in registers
                             (step t of row i-t as row i arrives); one launch per pass, no shared
                             memory.  k in {4, 6, 8, 10, 12} for FP32, {2, 3, 4, 6} for FP64
-                            (J2D_ERR_ARG otherwise).  Forward runs of single five-point grids
-                            only (adjoint runs take TILES, batches TILES, box plans SKEWED). */
+                            (J2D_ERR_ARG otherwise; default 8 and 2).  Forward runs of single
+                            five-point grids only (adjoint runs take TILES, batches TILES, box
+                            plans SKEWED).  AUTO takes it for FP32 grids too large for the chip. */
 } j2d_algo;
 
 /* Plan options (j2d5pt_set_option / j2d5pt_get_option). */
@@ -182,7 +183,9 @@ j2d_status j2d5pt_run_host(j2d5pt_plan_t plan, const void *h_in, void *h_out, lo
  * measured faster than blocked kernels storing each step); a plan set to a
  * temporally blocked algorithm stores each state from its one persistent
  * launch (the skewed and two-step FP32 schedules run as single-step tiles
- * here).  Single-grid, five-point plans; `in` must not lie
+ * here); a plan set to J2D_ALGO_STREAM stores every step's rows from its
+ * pipeline, one launch per pass of k steps (k in {2, 3, 4} for FP64, {4, 8}
+ * for FP32; other depths take 2 and 8).  Single-grid, five-point plans; `in` must not lie
  * inside `states`; steps >= 1.  J2D_ERR_ARG / J2D_ERR_ALIGN /
  * J2D_ERR_UNSUPPORTED as for j2d5pt_run. */
 j2d_status j2d5pt_run_states(j2d5pt_plan_t plan, const void *in, void *states, long steps, void *stream);

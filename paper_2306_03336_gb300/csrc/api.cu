@@ -637,10 +637,29 @@ extern "C" j2d_status j2d5pt_run_states(j2d5pt_plan_t p, const void *in, void *s
     }
     return J2D_OK;
   }
-  if (c.algo == J2D_ALGO_SKEWED || c.algo == J2D_ALGO_STREAM || c.sweep == 2) {
-    // the skewed, stream and two-step sweeps hold no whole state of a strip
-    // between their steps: single-step tiles (the plan's depth and shape if it
-    // chose tiles)
+  if (c.algo == J2D_ALGO_STREAM) {
+    // the stream schedule stores every step's rows from its pipeline: passes
+    // of k steps, pass j reading the state before it and writing its k states
+    const int depth = stream_keep_ok(p->dtype, c.depth) ? c.depth : (p->dtype == J2D_F64 ? 2 : 8);
+    const StreamGeom q = stream_geometry(p->dtype, g, depth, p->sms);
+    const long passes = (steps + q.depth - 1) / q.depth;
+    const void *src = in;
+    long s0 = 0;  // states before this pass
+    for (long j = 0; j < passes; ++j) {
+      const int m = (int)(j == 0 ? steps - (passes - 1) * q.depth : q.depth);
+      char *keep = st0 + (size_t)s0 * sb;
+      if ((e = launch_stream_pass(p->dtype, src, keep + (size_t)(m - 1) * sb, g, q, m, int_path_of(p), p->d_status,
+                                  s, keep, se)) != cudaSuccess)
+        return cuda_fail(e, "run_states: stream launch");
+      src = keep + (size_t)(m - 1) * sb;
+      s0 += m;
+    }
+    return J2D_OK;
+  }
+  if (c.algo == J2D_ALGO_SKEWED || c.sweep == 2) {
+    // the skewed and two-step sweeps hold no whole state of a strip between
+    // their steps: single-step tiles (the plan's depth and shape if it chose
+    // tiles)
     DtbRequest rq;
     rq.algo = J2D_ALGO_TILES;
     rq.depth = c.algo == J2D_ALGO_TILES ? p->opt_depth : 0;

@@ -85,9 +85,10 @@ struct StreamGeom {
 };
 int stream_max_depth(j2d_dtype dt);
 bool stream_depth_ok(j2d_dtype dt, int m);  // a kernel of m steps per pass exists
+bool stream_keep_ok(j2d_dtype dt, int m);   // ... and one that keeps every state
 StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms);
 cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const GridDesc &g, const StreamGeom &q, int m,
-                               int ipath, int *status, cudaStream_t s);
+                               int ipath, int *status, cudaStream_t s, void *keep = nullptr, long keep_stride = 0);
 
 cudaError_t measure_fma(j2d_dtype dt, double *rate);
 cudaError_t measure_exact(double *rate);

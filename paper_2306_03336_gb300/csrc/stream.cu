@@ -63,6 +63,8 @@ struct StreamParams {
   int H;        // rows stored per run
   int runs;     // runs per band
   int meff;     // steps of this pass (<= M: steps t > meff leave rows unchanged)
+  void *keep;   // keeping every state: step t's rows go to keep + (t - 1) * keep_stride
+  long keep_stride;
   int ipath;    // FP64: integer path on
   long nelem;   // elements of each buffer ((ny + 2) * pitch), for the checked build
   int *status;  // checked build: J2D_ERR_BOUNDS is recorded here
@@ -178,7 +180,8 @@ __device__ __forceinline__ bool stream_ok(long e, int V, const StreamParams &p) 
 
 // The pipeline of one warp: for each step t = 0..M-1 the two most recent rows
 // of step t (A: the older, B: the newer).
-template <typename T, int M, bool EDGE, bool IP> struct Pipe {
+// KEEP: every step's rows are stored (to p.keep), not only the last step's.
+template <typename T, int M, bool EDGE, bool IP, bool KEEP> struct Pipe {
   using R = typename RowOf<T>::R;
   using W = typename RowOf<T>::W;
   R A[M], B[M];
@@ -218,9 +221,13 @@ template <typename T, int M, bool EDGE, bool IP> struct Pipe {
       A[t - 1] = B[t - 1];
       B[t - 1] = cur;
       cur = n;
+      if (KEEP && t <= p.meff && st && r >= y0 && r < y1) {
+        const long e = (long)r * p.pitch + e0;
+        if (stream_ok(e, VecOf<T>::V, p)) row_store(static_cast<T *>(p.keep) + (t - 1) * p.keep_stride + e, n);
+      }
     }
     const int r = i - M;
-    if (st && r >= y0 && r < y1) {
+    if (!KEEP && st && r >= y0 && r < y1) {
       const long e = (long)r * p.pitch + e0;
       if (stream_ok(e, VecOf<T>::V, p)) row_store(out + e, cur);
     }
@@ -271,7 +278,7 @@ __device__ __forceinline__ RowD read_slot(const float4 *q, RowD *) {
   return {v.x, v.y};
 }
 
-template <typename T, int M, bool EDGE, bool IP>
+template <typename T, int M, bool EDGE, bool IP, bool KEEP>
 __device__ __forceinline__ void stream_sweep(const StreamParams &p, const typename RowOf<T>::W &k, long e0, int x0,
                                              unsigned hold, bool live, bool st, int y0, int y1, float4 *ring) {
   using R = typename RowOf<T>::R;
@@ -280,7 +287,7 @@ __device__ __forceinline__ void stream_sweep(const StreamParams &p, const typena
   static_assert(S >= kAhead + 2 && S <= kStageMax, "ring too small");
   const T *in = static_cast<const T *>(p.in);
   T *out = static_cast<T *>(p.out);
-  Pipe<T, M, EDGE, IP> pipe(k, p, out, e0, x0, hold, st, y0, y1);
+  Pipe<T, M, EDGE, IP, KEEP> pipe(k, p, out, e0, x0, hold, st, y0, y1);
   int a = max(y0 - M, 0);  // earlier rows only warm the pipeline up
   if (U == 4) a &= ~3;
   const int iend = y1 + M;  // the last iteration stores row y1 - 1
@@ -328,7 +335,7 @@ __device__ __forceinline__ void make_weights(const StreamParams &p, WeightsD *k)
   k->u = exact_weights(k->l);
 }
 
-template <typename T, int M, bool IP>
+template <typename T, int M, bool IP, bool KEEP>
 __global__ void __launch_bounds__(32 * WarpsOf<T>::W) stream_kernel(StreamParams p) {
   constexpr int V = VecOf<T>::V;
   const int lane = threadIdx.x & 31;
@@ -354,34 +361,43 @@ __global__ void __launch_bounds__(32 * WarpsOf<T>::W) stream_kernel(StreamParams
   __shared__ float4 ring[WarpsOf<T>::W][2 * TripOf<T>::U * 32];
   float4 *mine = &ring[threadIdx.x >> 5][lane];
   if (edge)
-    stream_sweep<T, M, true, IP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
+    stream_sweep<T, M, true, IP, KEEP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
   else
-    stream_sweep<T, M, false, IP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
+    stream_sweep<T, M, false, IP, KEEP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
 }
 
 // ---- host side ------------------------------------------------------------------
 
 using StreamFn = void (*)(StreamParams);
 
-template <typename T, bool IP, int... Ms> struct StreamTable;
-template <typename T, bool IP> struct StreamTable<T, IP> {
+template <typename T, bool IP, bool KEEP, int... Ms> struct StreamTable;
+template <typename T, bool IP, bool KEEP> struct StreamTable<T, IP, KEEP> {
   static StreamFn get(int) { return nullptr; }
 };
-template <typename T, bool IP, int M0, int... Ms> struct StreamTable<T, IP, M0, Ms...> {
-  static StreamFn get(int m) { return m == M0 ? stream_kernel<T, M0, IP> : StreamTable<T, IP, Ms...>::get(m); }
+template <typename T, bool IP, bool KEEP, int M0, int... Ms> struct StreamTable<T, IP, KEEP, M0, Ms...> {
+  static StreamFn get(int m) {
+    return m == M0 ? stream_kernel<T, M0, IP, KEEP> : StreamTable<T, IP, KEEP, Ms...>::get(m);
+  }
 };
 
 int stream_max_depth(j2d_dtype dt) { return dt == J2D_F64 ? kStreamMaxF64 : kStreamMaxF32; }
 
 // Steps per pass with a kernel of their own; a run's shorter pass runs the
-// kernel of the run's depth with fewer steps.
-static StreamFn stream_fn(j2d_dtype dt, int m, int ipath) {
-  if (dt == J2D_F64)
-    return ipath ? StreamTable<double, true, 2, 3, 4, 6>::get(m) : StreamTable<double, false, 2, 3, 4, 6>::get(m);
-  return StreamTable<float, false, 4, 6, 8, 10, 12>::get(m);
+// kernel of the run's depth with fewer steps.  Runs that keep every state
+// have kernels for fewer depths.
+static StreamFn stream_fn(j2d_dtype dt, int m, int ipath, bool keep = false) {
+  if (dt == J2D_F64) {
+    if (keep)
+      return ipath ? StreamTable<double, true, true, 2, 3, 4>::get(m) : StreamTable<double, false, true, 2, 3, 4>::get(m);
+    return ipath ? StreamTable<double, true, false, 2, 3, 4, 6>::get(m)
+                 : StreamTable<double, false, false, 2, 3, 4, 6>::get(m);
+  }
+  if (keep) return StreamTable<float, false, true, 4, 8>::get(m);
+  return StreamTable<float, false, false, 4, 6, 8, 10, 12>::get(m);
 }
 
 bool stream_depth_ok(j2d_dtype dt, int m) { return stream_fn(dt, m, 1) != nullptr; }
+bool stream_keep_ok(j2d_dtype dt, int m) { return stream_fn(dt, m, 1, true) != nullptr; }
 
 // Resident blocks per SM of one instantiation (cached).
 static int stream_occupancy(j2d_dtype dt, int m) {
@@ -419,9 +435,11 @@ StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) 
   return q;
 }
 
-// A pass of m <= q.depth steps, in -> out (distinct buffers whose rings agree).
+// A pass of m <= q.depth steps, in -> out (distinct buffers whose rings
+// agree); with keep set, step t's state goes to keep + (t - 1) * keep_stride
+// elements instead (out unused).
 cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const GridDesc &g, const StreamGeom &q, int m,
-                               int ipath, int *status, cudaStream_t s) {
+                               int ipath, int *status, cudaStream_t s, void *keep, long keep_stride) {
   StreamParams p;
   p.in = in;
   p.out = out;
@@ -435,11 +453,13 @@ cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const Gr
   p.H = q.H;
   p.runs = q.runs;
   p.meff = m;
+  p.keep = keep;
+  p.keep_stride = keep_stride;
   p.ipath = ipath;
   p.nelem = (long)(g.ny + 2) * g.pitch;
   p.status = status;
   for (int i = 0; i < 5; ++i) p.w[i] = g.w[i];
-  StreamFn fn = stream_fn(dt, q.depth, ipath);
+  StreamFn fn = stream_fn(dt, q.depth, ipath, keep != nullptr);
   if (!fn || m < 1 || m > q.depth) return cudaErrorInvalidValue;
   const long units = (long)q.bands * q.runs;
   const int W = stream_warps(dt);

@@ -1,7 +1,9 @@
 """The state-keeping forward run (j2d5pt_run_states): every intermediate
 state, ring included, bit for bit equal to chained single-step runs of the
 one-step kernel, for every algorithm (the skewed and two-step FP32
-schedules run as single-step tiles there), ragged sizes, depths that do and
+schedules run as single-step tiles there; the stream schedule stores every
+step from its pipeline, also at depths without a state-keeping kernel of
+their own, which take the default depth), ragged sizes, depths that do and
 do not divide the step count; the oracle on one case; argument errors."""
 import numpy as np
 import pytest
@@ -51,7 +53,8 @@ def _states(nx, ny, dtype, w, u0, steps, algo, depth, wx):
 
 
 CONFIGS = [("onestep", 0, 0), ("tiles", 1, 2), ("tiles", 3, 4), ("tiles", 4, 1), ("tiles", 7, 8), ("bands", 3, 0),
-           ("resident", 0, 0), ("skewed", 4, 4), ("auto", 0, 0)]
+           ("resident", 0, 0), ("skewed", 4, 4), ("stream", 2, 0), ("stream", 3, 0), ("stream", 4, 0),
+           ("stream", 6, 0), ("auto", 0, 0)]
 
 
 @pytest.mark.parametrize("algo,depth,wx", CONFIGS)
@@ -67,7 +70,7 @@ def test_states_bitwise_f64(algo, depth, wx, nx, ny):
 
 
 @pytest.mark.parametrize("algo,depth,wx", [("tiles", 8, 2), ("tiles", 3, 4), ("bands", 5, 0), ("resident", 0, 0),
-                                           ("skewed", 8, 4)])
+                                           ("skewed", 8, 4), ("stream", 4, 0), ("stream", 8, 0), ("stream", 12, 0)])
 @pytest.mark.parametrize("nx,ny", [(300, 200), (513, 31), (7, 9)])
 def test_states_bitwise_f32(algo, depth, wx, nx, ny):
     # FP32 tiles would sweep two steps per pass; a state-keeping run takes one
