@@ -151,3 +151,44 @@ def test_random_batch(i):
         q.sync()
         assert np.array_equal(outs[g], q.to_host(b)), (i, g, nx, ny, dt, steps, depth, wx, algo)
         q.close()
+
+
+N_STREAM = 60
+
+
+@pytest.mark.parametrize("i", range(N_STREAM))
+def test_random_stream_configuration(i):
+    """The stream schedule on seeded random sizes (thin, ragged, a band or
+    many), step counts around and across whole passes, and every depth it
+    has a kernel for, forward, in place or not: bit-identical to the one-step
+    kernel and within the oracle bounds."""
+    r = np.random.Generator(np.random.PCG64(2306034200 + i))
+    dt = str(r.choice(["f64", "f32"]))
+    depth = int(r.choice([2, 3, 4, 6] if dt == "f64" else [4, 6, 8, 10, 12]))
+    nx = int(r.choice([1, 2, 3, 59, 60, 61, 64, 112, 113, 128, 500]) if r.random() < 0.5 else r.integers(1, 901))
+    ny = int(r.integers(1, 601))
+    steps = int(r.choice([1, depth - 1, depth, depth + 1, 2 * depth, 3 * depth + 2, 17]))
+    steps = max(steps, 1)
+    alias = bool(r.random() < 0.25)
+    seed = 2306034300 + i
+    u0 = synth.field(nx, ny, seed)
+    w = synth.weights(seed + 1)
+    p = j2d5pt.Plan(nx, ny, dt, w)
+    src = p.to_device(u0 if dt == "f64" else u0.astype(np.float32))
+    p.set("algo", "onestep")
+    ref_dev = p.empty()
+    p.run(src, ref_dev, steps)
+    p.sync()
+    ref = p.to_host(ref_dev)
+    p.set("algo", "stream").set("depth", depth)
+    out = src if alias else p.empty()
+    p.run(src, out, steps)
+    p.sync()
+    got = p.to_host(out)
+    p.close()
+    case = (dt, depth, nx, ny, steps, alias)
+    assert np.array_equal(got, ref), (case, int(np.count_nonzero(got != ref)))
+    if dt == "f64":
+        assert rel_err(got, oracle.run(u0, w, steps)) <= TOL_F64, case
+    else:
+        assert rel_err(got, oracle.run_f32(u0.astype(np.float32).astype(np.float64), w, steps)) <= f32_bound(steps), case

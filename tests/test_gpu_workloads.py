@@ -52,7 +52,8 @@ def headline():
     return u0, w, steps, oracle.run(u0, w, steps, threads=oracle.max_threads())
 
 
-@pytest.mark.parametrize("algo,depth", [("resident", 0), ("bands", 32), ("bands", 8), ("tiles", 4), ("onestep", 0)])
+@pytest.mark.parametrize("algo,depth", [("resident", 0), ("bands", 32), ("bands", 8), ("tiles", 4), ("onestep", 0),
+                                        ("stream", 2), ("stream", 6)])
 def test_headline_workload_full_grid(headline, algo, depth):
     u0, w, steps, ref = headline
     p, dst = _run(u0, w, steps, "f64", algo, depth)
@@ -111,15 +112,15 @@ def test_16384_f64_full_grid_bitwise_and_oracle_blocks():
     u0 = synth.field(n, n, synth.data_seed(1))
     w = synth.weights(synth.weight_seed(1))
     _full_size_case(u0, w, steps, "f64", [("tiles", 4, 4), ("tiles", 4, 2), ("bands", 8, 0), ("skewed", 8, 4),
-                                          ("skewed", 16, 8)], TOL_F64)
+                                          ("skewed", 16, 8), ("stream", 2, 0), ("stream", 3, 0)], TOL_F64)
 
 
 def test_16384_f32_full_grid_bitwise_and_oracle_blocks():
     n, steps = 16384, 1000
     u0 = synth.field(n, n, synth.data_seed(1))
     w = synth.weights(synth.weight_seed(1))
-    _full_size_case(u0, w, steps, "f32", [("tiles", 16, 2), ("tiles", 16, 4), ("skewed", 16, 4), ("skewed", 24, 8)],
-                    f32_bound(steps))
+    _full_size_case(u0, w, steps, "f32", [("tiles", 16, 2), ("tiles", 16, 4), ("skewed", 16, 4), ("skewed", 24, 8),
+                                          ("stream", 8, 0), ("stream", 12, 0)], f32_bound(steps))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -130,5 +131,5 @@ def test_paper_domain_8592x8328(dtype):
     u0 = synth.field(nx, ny, synth.data_seed(1) + 20)
     w = synth.weights(synth.weight_seed(1))
     tol = TOL_F64 if dtype == "f64" else f32_bound(steps)
-    _full_size_case(u0, w, steps, dtype, [("tiles", 4, 4), ("skewed", 8, 4)] if dtype == "f64"
-                    else [("tiles", 16, 4), ("skewed", 16, 4)], tol)
+    _full_size_case(u0, w, steps, dtype, [("tiles", 4, 4), ("skewed", 8, 4), ("stream", 2, 0)] if dtype == "f64"
+                    else [("tiles", 16, 4), ("skewed", 16, 4), ("stream", 8, 0)], tol)
