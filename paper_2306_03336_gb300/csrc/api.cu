@@ -366,8 +366,9 @@ static j2d_status run_dtb(j2d5pt_plan_t p, const void *const *in, void *const *o
 static j2d_status run_grid_stream(j2d5pt_plan_t p, int gi, const void *in, void *out, long steps, int depth,
                                   cudaStream_t s) {
   const GridDesc &g = p->grids[gi];
-  if (!stream_depth_ok(p->dtype, depth))
-    return fail(J2D_ERR_ARG, "run: no stream kernel of depth %d for %s", depth, p->dtype == J2D_F64 ? "f64" : "f32");
+  if (!stream_depth_ok(p->dtype, depth, g.shape))
+    return fail(J2D_ERR_ARG, "run: no stream kernel of depth %d for %s%s", depth, p->dtype == J2D_F64 ? "f64" : "f32",
+                g.shape == 9 ? " box" : "");
   const StreamGeom q = stream_geometry(p->dtype, g, depth, p->sms);
   const long passes = (steps + q.depth - 1) / q.depth;
   const int first = (int)(steps - (passes - 1) * q.depth);
@@ -777,9 +778,9 @@ static j2d_status autotune_common(j2d5pt_plan_t p, const void *const *in, void *
       for (int wx : {1, 2, 4}) cands.push_back({J2D_ALGO_TILES, d, wx});
     for (int wx : {2, 4, 8}) cands.push_back({J2D_ALGO_SKEWED, d, wx});
   }
-  if (single && !box)
+  if (single)
     for (int d = 1; d <= stream_max_depth(p->dtype) && d <= steps; ++d)
-      if (stream_depth_ok(p->dtype, d)) cands.push_back({J2D_ALGO_STREAM, d, 0});
+      if (stream_depth_ok(p->dtype, d, p->grids[0].shape)) cands.push_back({J2D_ALGO_STREAM, d, 0});
   float best_ms = 1e30f;
   Cand best = {J2D_ALGO_AUTO, 0, 0};
   cudaEvent_t e0, e1;

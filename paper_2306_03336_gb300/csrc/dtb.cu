@@ -1870,16 +1870,17 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
     if (rq.steps < 4) algo = J2D_ALGO_ONESTEP;
     else if (fits && (single || dt == J2D_F64)) algo = J2D_ALGO_RESIDENT;  // FP64 batches: grouped resident
     // FP32 grids too large for the chip: the stream schedule (16384^2: 3820
-    // GCells/s against 1950 for the best shared-memory schedule)
-    else if (single && dt == J2D_F32 && !rq.adjoint && grids[0].shape == 5) algo = J2D_ALGO_STREAM;
+    // GCells/s against 1950 for the best shared-memory schedule; the box 2397
+    // against 1418)
+    else if (single && dt == J2D_F32 && !rq.adjoint) algo = J2D_ALGO_STREAM;
     else algo = J2D_ALGO_TILES;
   }
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
   if (algo == J2D_ALGO_BANDS && !single) algo = J2D_ALGO_TILES;
   if (algo == J2D_ALGO_SKEWED && rq.adjoint) algo = J2D_ALGO_TILES;  // the skewed order is forward only
   if (algo == J2D_ALGO_STREAM && (rq.adjoint || !single)) algo = J2D_ALGO_TILES;  // forward, one grid
-  // the 3x3 box runs the one-step kernel or the skewed tiles
-  if (grids[0].shape == 9 && algo != J2D_ALGO_ONESTEP) algo = J2D_ALGO_SKEWED;
+  // the 3x3 box runs the one-step kernel, the skewed tiles or the stream schedule
+  if (grids[0].shape == 9 && algo != J2D_ALGO_ONESTEP && algo != J2D_ALGO_STREAM) algo = J2D_ALGO_SKEWED;
   c.algo = algo;
   c.depth = rq.depth > 0 ? rq.depth : (dt == J2D_F64 ? 4 : 8);
   c.tile_wx = rq.tile_wx > 0 ? rq.tile_wx : (dt == J2D_F64 ? 4 : 2);
@@ -1890,7 +1891,7 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
     c.sweep = 2;
     c.rows = dtb_rows_max_pair(dt, smem_optin);
   }
-  if (algo == J2D_ALGO_STREAM && rq.depth <= 0) c.depth = dt == J2D_F64 ? 2 : 8;
+  if (algo == J2D_ALGO_STREAM && rq.depth <= 0) c.depth = dt == J2D_F64 ? 2 : (grids[0].shape == 9 ? 4 : 8);
   if (algo == J2D_ALGO_SKEWED) {
     c.rows = dtb_rows_max_skew(dt, smem_optin);
     if (rq.depth <= 0) c.depth = dt == J2D_F64 ? 8 : 16;

@@ -84,7 +84,7 @@ struct StreamGeom {
   int runs = 0;   // runs per band
 };
 int stream_max_depth(j2d_dtype dt);
-bool stream_depth_ok(j2d_dtype dt, int m);  // a kernel of m steps per pass exists
+bool stream_depth_ok(j2d_dtype dt, int m, int shape = 5);  // a kernel of m steps per pass exists
 bool stream_keep_ok(j2d_dtype dt, int m);   // ... and one that keeps every state
 StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms);
 cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const GridDesc &g, const StreamGeom &q, int m,

@@ -68,7 +68,7 @@ struct StreamParams {
   int ipath;    // FP64: integer path on
   long nelem;   // elements of each buffer ((ny + 2) * pitch), for the checked build
   int *status;  // checked build: J2D_ERR_BOUNDS is recorded here
-  double w[5];  // W, E, S, C, N
+  double w[9];  // five-point: W, E, S, C, N; box: the nine weights, rows y-1, y, y+1, columns x-1, x, x+1
 };
 
 // ---- one lane's 16-byte vector of a row, in registers -------------------------
@@ -154,9 +154,103 @@ __device__ __forceinline__ RowD row_step(const WeightsD &k, const RowD &ym, cons
   return {stencil_cell(k.l, k.u, ea, L, c.b, ym.a, c.a, yp.a), stencil_cell(k.l, k.u, eb, c.a, R, ym.b, c.b, yp.b)};
 }
 
-template <typename T> struct RowOf;
-template <> struct RowOf<float> { using R = RowF; using W = WeightsF; };
-template <> struct RowOf<double> { using R = RowD; using W = WeightsD; };
+// ---- the 3x3 box (j2d9pt): every row also carries its outer neighbours ---------
+// A box cell reads the x - 1 and x + 1 columns of all three rows, so a row's
+// two values beyond the lane (L: column x0 - 1, R: the column after the
+// lane's last) are taken by shuffles once, when the row is produced, and
+// travel with it through the three steps that read it.  The chain order is
+// that of stencil_box() in common.cuh.
+struct RowF9 {
+  float2 a, b;  // (v0, v2), (v1, v3) as in RowF
+  float L, R;
+};
+struct WeightsF9 {
+  float2 w[9];  // Box9 chain order, each weight in both halves
+};
+struct RowD9 {
+  double a, b, L, R;
+};
+struct WeightsD9 {
+  Box9<double> b;
+  ExactWN<9> u;
+};
+
+__device__ __forceinline__ RowF9 row_zero(RowF9 *) { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f}; }
+__device__ __forceinline__ RowD9 row_zero(RowD9 *) { return {0.0, 0.0, 0.0, 0.0}; }
+__device__ __forceinline__ void row_nbrs(RowF9 &r) {
+  r.L = __shfl_up_sync(0xffffffffu, r.b.y, 1);
+  r.R = __shfl_down_sync(0xffffffffu, r.a.x, 1);
+}
+__device__ __forceinline__ void row_nbrs(RowD9 &r) {
+  r.L = __shfl_up_sync(0xffffffffu, r.b, 1);
+  r.R = __shfl_down_sync(0xffffffffu, r.a, 1);
+}
+__device__ __forceinline__ void row_store(float *p, const RowF9 &r) {
+  *reinterpret_cast<float4 *>(p) = make_float4(r.a.x, r.b.x, r.a.y, r.b.y);
+}
+__device__ __forceinline__ void row_store(double *p, const RowD9 &r) {
+  *reinterpret_cast<double2 *>(p) = make_double2(r.a, r.b);
+}
+__device__ __forceinline__ RowF9 row_hold(RowF9 n, const RowF9 &c, unsigned m) {
+  if (m & 1u) n.a.x = c.a.x;
+  if (m & 2u) n.b.x = c.b.x;
+  if (m & 4u) n.a.y = c.a.y;
+  if (m & 8u) n.b.y = c.b.y;
+  return n;
+}
+__device__ __forceinline__ RowD9 row_hold(RowD9 n, const RowD9 &c, unsigned m) {
+  if (m & 1u) n.a = c.a;
+  if (m & 2u) n.b = c.b;
+  return n;
+}
+
+// Terms in chain order: (y-1, x), (y-1, x-1), (y-1, x+1), (y, x), (y, x-1),
+// (y, x+1), (y+1, x), (y+1, x-1), (y+1, x+1).  For the pair (v0, v2) the
+// x - 1 operands (L, v1) mix the pairs and take scalar FMAs, the x + 1
+// operands are the pair (v1, v3); for (v1, v3) the x - 1 operands are
+// (v0, v2) and the x + 1 operands (v2, R) take scalar FMAs.
+__device__ __forceinline__ RowF9 row_step9(const WeightsF9 &k, const RowF9 &ym, const RowF9 &c, const RowF9 &yp) {
+  float2 ra = __fmul2_rn(k.w[0], ym.a);
+  ra.x = __fmaf_rn(k.w[1].x, ym.L, ra.x);
+  ra.y = __fmaf_rn(k.w[1].x, ym.b.x, ra.y);
+  ra = __ffma2_rn(k.w[2], ym.b, ra);
+  ra = __ffma2_rn(k.w[3], c.a, ra);
+  ra.x = __fmaf_rn(k.w[4].x, c.L, ra.x);
+  ra.y = __fmaf_rn(k.w[4].x, c.b.x, ra.y);
+  ra = __ffma2_rn(k.w[5], c.b, ra);
+  ra = __ffma2_rn(k.w[6], yp.a, ra);
+  ra.x = __fmaf_rn(k.w[7].x, yp.L, ra.x);
+  ra.y = __fmaf_rn(k.w[7].x, yp.b.x, ra.y);
+  ra = __ffma2_rn(k.w[8], yp.b, ra);
+  float2 rb = __fmul2_rn(k.w[0], ym.b);
+  rb = __ffma2_rn(k.w[1], ym.a, rb);
+  rb.x = __fmaf_rn(k.w[2].x, ym.a.y, rb.x);
+  rb.y = __fmaf_rn(k.w[2].x, ym.R, rb.y);
+  rb = __ffma2_rn(k.w[3], c.b, rb);
+  rb = __ffma2_rn(k.w[4], c.a, rb);
+  rb.x = __fmaf_rn(k.w[5].x, c.a.y, rb.x);
+  rb.y = __fmaf_rn(k.w[5].x, c.R, rb.y);
+  rb = __ffma2_rn(k.w[6], yp.b, rb);
+  rb = __ffma2_rn(k.w[7], yp.a, rb);
+  rb.x = __fmaf_rn(k.w[8].x, yp.a.y, rb.x);
+  rb.y = __fmaf_rn(k.w[8].x, yp.R, rb.y);
+  return {ra, rb, 0.f, 0.f};
+}
+__device__ __forceinline__ RowD9 row_step9(const WeightsD9 &k, const RowD9 &ym, const RowD9 &c, const RowD9 &yp,
+                                           bool ea, bool eb) {
+  return {stencil_box_cell(k.b, k.u, ea, ym.L, ym.a, ym.b, c.L, c.a, c.b, yp.L, yp.a, yp.b),
+          stencil_box_cell(k.b, k.u, eb, ym.a, ym.b, ym.R, c.a, c.b, c.R, yp.a, yp.b, yp.R), 0.0, 0.0};
+}
+
+template <typename T, int SH> struct RowOf;
+template <> struct RowOf<float, 5> { using R = RowF; using W = WeightsF; };
+template <> struct RowOf<double, 5> { using R = RowD; using W = WeightsD; };
+template <> struct RowOf<float, 9> { using R = RowF9; using W = WeightsF9; };
+template <> struct RowOf<double, 9> { using R = RowD9; using W = WeightsD9; };
+
+// Five-point rows take their neighbours when they are read.
+__device__ __forceinline__ void row_nbrs(RowF &) {}
+__device__ __forceinline__ void row_nbrs(RowD &) {}
 
 // ea, eb: the lane's first / second cell takes the integer path (FP64; known
 // at compile time where the trip's row phases are: the column parities of a
@@ -168,6 +262,14 @@ __device__ __forceinline__ RowF step_any(const WeightsF &k, const RowF &ym, cons
 __device__ __forceinline__ RowD step_any(const WeightsD &k, const RowD &ym, const RowD &c, const RowD &yp, bool ea,
                                          bool eb) {
   return row_step(k, ym, c, yp, ea, eb);
+}
+__device__ __forceinline__ RowF9 step_any(const WeightsF9 &k, const RowF9 &ym, const RowF9 &c, const RowF9 &yp, bool,
+                                          bool) {
+  return row_step9(k, ym, c, yp);
+}
+__device__ __forceinline__ RowD9 step_any(const WeightsD9 &k, const RowD9 &ym, const RowD9 &c, const RowD9 &yp,
+                                          bool ea, bool eb) {
+  return row_step9(k, ym, c, yp, ea, eb);
 }
 
 // In the checked build, is [e, e + V) inside the buffer of nelem elements?
@@ -181,9 +283,9 @@ __device__ __forceinline__ bool stream_ok(long e, int V, const StreamParams &p) 
 // The pipeline of one warp: for each step t = 0..M-1 the two most recent rows
 // of step t (A: the older, B: the newer).
 // KEEP: every step's rows are stored (to p.keep), not only the last step's.
-template <typename T, int M, bool EDGE, bool IP, bool KEEP> struct Pipe {
-  using R = typename RowOf<T>::R;
-  using W = typename RowOf<T>::W;
+template <typename T, int M, bool EDGE, bool IP, bool KEEP, int SH> struct Pipe {
+  using R = typename RowOf<T, SH>::R;
+  using W = typename RowOf<T, SH>::W;
   R A[M], B[M];
   const W &k;
   const StreamParams &p;
@@ -218,6 +320,7 @@ template <typename T, int M, bool EDGE, bool IP, bool KEEP> struct Pipe {
       R n = step_any(k, A[t - 1], B[t - 1], cur, IP && exact_cell(1, yy, true), IP && exact_cell(0, yy, true));
       if (EDGE) n = row_hold(n, B[t - 1], hold);
       if (CHK && (r == 0 || r == p.ny + 1 || t > p.meff)) n = B[t - 1];
+      if (SH == 9 && t < M) row_nbrs(n);  // read with its neighbours by steps t + 1 (three times)
       A[t - 1] = B[t - 1];
       B[t - 1] = cur;
       cur = n;
@@ -273,21 +376,33 @@ __device__ __forceinline__ RowF read_slot(const float4 *q, RowF *) {
   const float4 v = *q;
   return {make_float2(v.x, v.z), make_float2(v.y, v.w)};
 }
+__device__ __forceinline__ RowF9 read_slot(const float4 *q, RowF9 *) {
+  const float4 v = *q;
+  RowF9 r = {make_float2(v.x, v.z), make_float2(v.y, v.w), 0.f, 0.f};
+  row_nbrs(r);
+  return r;
+}
+__device__ __forceinline__ RowD9 read_slot(const float4 *q, RowD9 *) {
+  const double2 v = *reinterpret_cast<const double2 *>(q);
+  RowD9 r = {v.x, v.y, 0.0, 0.0};
+  row_nbrs(r);
+  return r;
+}
 __device__ __forceinline__ RowD read_slot(const float4 *q, RowD *) {
   const double2 v = *reinterpret_cast<const double2 *>(q);
   return {v.x, v.y};
 }
 
-template <typename T, int M, bool EDGE, bool IP, bool KEEP>
-__device__ __forceinline__ void stream_sweep(const StreamParams &p, const typename RowOf<T>::W &k, long e0, int x0,
+template <typename T, int M, bool EDGE, bool IP, bool KEEP, int SH>
+__device__ __forceinline__ void stream_sweep(const StreamParams &p, const typename RowOf<T, SH>::W &k, long e0, int x0,
                                              unsigned hold, bool live, bool st, int y0, int y1, float4 *ring) {
-  using R = typename RowOf<T>::R;
+  using R = typename RowOf<T, SH>::R;
   constexpr int U = TripOf<T>::U;
   constexpr int S = 2 * U;  // slots
   static_assert(S >= kAhead + 2 && S <= kStageMax, "ring too small");
   const T *in = static_cast<const T *>(p.in);
   T *out = static_cast<T *>(p.out);
-  Pipe<T, M, EDGE, IP, KEEP> pipe(k, p, out, e0, x0, hold, st, y0, y1);
+  Pipe<T, M, EDGE, IP, KEEP, SH> pipe(k, p, out, e0, x0, hold, st, y0, y1);
   int a = max(y0 - M, 0);  // earlier rows only warm the pipeline up
   if (U == 4) a &= ~3;
   const int iend = y1 + M;  // the last iteration stores row y1 - 1
@@ -330,12 +445,21 @@ __device__ __forceinline__ void make_weights(const StreamParams &p, WeightsF *k)
   k->c = make_float2(c, c);
   k->n = make_float2(n, n);
 }
+__device__ __forceinline__ void make_weights(const StreamParams &p, WeightsF9 *k) {
+  const Box9<float> b = box_chain<float>(p.w);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) k->w[i] = make_float2(b.w[i], b.w[i]);
+}
+__device__ __forceinline__ void make_weights(const StreamParams &p, WeightsD9 *k) {
+  k->b = box_chain<double>(p.w);
+  k->u = box_exact_weights(k->b);
+}
 __device__ __forceinline__ void make_weights(const StreamParams &p, WeightsD *k) {
   k->l = Links<double>{p.w[0], p.w[1], p.w[2], p.w[3], p.w[4]};
   k->u = exact_weights(k->l);
 }
 
-template <typename T, int M, bool IP, bool KEEP>
+template <typename T, int M, bool IP, bool KEEP, int SH>
 __global__ void __launch_bounds__(32 * WarpsOf<T>::W) stream_kernel(StreamParams p) {
   constexpr int V = VecOf<T>::V;
   const int lane = threadIdx.x & 31;
@@ -356,27 +480,27 @@ __global__ void __launch_bounds__(32 * WarpsOf<T>::W) stream_kernel(StreamParams
     if (x0 + v == 0 || x0 + v == p.nx + 1) hold |= 1u << v;
   const bool edge = __any_sync(0xffffffffu, hold != 0);
   const int y0 = 1 + run * p.H, y1 = min(y0 + p.H, p.ny + 1);
-  typename RowOf<T>::W k;
+  typename RowOf<T, SH>::W k;
   make_weights(p, &k);
   __shared__ float4 ring[WarpsOf<T>::W][2 * TripOf<T>::U * 32];
   float4 *mine = &ring[threadIdx.x >> 5][lane];
   if (edge)
-    stream_sweep<T, M, true, IP, KEEP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
+    stream_sweep<T, M, true, IP, KEEP, SH>(p, k, e0, x0, hold, live, st, y0, y1, mine);
   else
-    stream_sweep<T, M, false, IP, KEEP>(p, k, e0, x0, hold, live, st, y0, y1, mine);
+    stream_sweep<T, M, false, IP, KEEP, SH>(p, k, e0, x0, hold, live, st, y0, y1, mine);
 }
 
 // ---- host side ------------------------------------------------------------------
 
 using StreamFn = void (*)(StreamParams);
 
-template <typename T, bool IP, bool KEEP, int... Ms> struct StreamTable;
-template <typename T, bool IP, bool KEEP> struct StreamTable<T, IP, KEEP> {
+template <typename T, bool IP, bool KEEP, int SH, int... Ms> struct StreamTable;
+template <typename T, bool IP, bool KEEP, int SH> struct StreamTable<T, IP, KEEP, SH> {
   static StreamFn get(int) { return nullptr; }
 };
-template <typename T, bool IP, bool KEEP, int M0, int... Ms> struct StreamTable<T, IP, KEEP, M0, Ms...> {
+template <typename T, bool IP, bool KEEP, int SH, int M0, int... Ms> struct StreamTable<T, IP, KEEP, SH, M0, Ms...> {
   static StreamFn get(int m) {
-    return m == M0 ? stream_kernel<T, M0, IP, KEEP> : StreamTable<T, IP, KEEP, Ms...>::get(m);
+    return m == M0 ? stream_kernel<T, M0, IP, KEEP, SH> : StreamTable<T, IP, KEEP, SH, Ms...>::get(m);
   }
 };
 
@@ -385,29 +509,37 @@ int stream_max_depth(j2d_dtype dt) { return dt == J2D_F64 ? kStreamMaxF64 : kStr
 // Steps per pass with a kernel of their own; a run's shorter pass runs the
 // kernel of the run's depth with fewer steps.  Runs that keep every state
 // have kernels for fewer depths.
-static StreamFn stream_fn(j2d_dtype dt, int m, int ipath, bool keep = false) {
+static StreamFn stream_fn(j2d_dtype dt, int m, int ipath, bool keep = false, int shape = 5) {
+  if (shape == 9) {  // the box: no state-keeping runs
+    if (keep) return nullptr;
+    if (dt == J2D_F64)
+      return ipath ? StreamTable<double, true, false, 9, 2, 3, 4>::get(m)
+                   : StreamTable<double, false, false, 9, 2, 3, 4>::get(m);
+    return StreamTable<float, false, false, 9, 4, 6, 8>::get(m);
+  }
   if (dt == J2D_F64) {
     if (keep)
-      return ipath ? StreamTable<double, true, true, 2, 3, 4>::get(m) : StreamTable<double, false, true, 2, 3, 4>::get(m);
-    return ipath ? StreamTable<double, true, false, 2, 3, 4, 6>::get(m)
-                 : StreamTable<double, false, false, 2, 3, 4, 6>::get(m);
+      return ipath ? StreamTable<double, true, true, 5, 2, 3, 4>::get(m)
+                   : StreamTable<double, false, true, 5, 2, 3, 4>::get(m);
+    return ipath ? StreamTable<double, true, false, 5, 2, 3, 4, 6>::get(m)
+                 : StreamTable<double, false, false, 5, 2, 3, 4, 6>::get(m);
   }
-  if (keep) return StreamTable<float, false, true, 4, 8>::get(m);
-  return StreamTable<float, false, false, 4, 6, 8, 10, 12>::get(m);
+  if (keep) return StreamTable<float, false, true, 5, 4, 8>::get(m);
+  return StreamTable<float, false, false, 5, 4, 6, 8, 10, 12>::get(m);
 }
 
-bool stream_depth_ok(j2d_dtype dt, int m) { return stream_fn(dt, m, 1) != nullptr; }
+bool stream_depth_ok(j2d_dtype dt, int m, int shape) { return stream_fn(dt, m, 1, false, shape) != nullptr; }
 bool stream_keep_ok(j2d_dtype dt, int m) { return stream_fn(dt, m, 1, true) != nullptr; }
 
 // Resident blocks per SM of one instantiation (cached).
-static int stream_occupancy(j2d_dtype dt, int m) {
+static int stream_occupancy(j2d_dtype dt, int m, int shape) {
   static std::mutex mu;
-  static int cache[2][16] = {};
+  static int cache[2][2][16] = {};
   std::lock_guard<std::mutex> lk(mu);
-  int &c = cache[dt == J2D_F64 ? 1 : 0][m];
+  int &c = cache[shape == 9 ? 1 : 0][dt == J2D_F64 ? 1 : 0][m];
   if (c == 0) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_fn(dt, m, 1), 32 * stream_warps(dt), 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_fn(dt, m, 1, false, shape), 32 * stream_warps(dt), 0) != cudaSuccess ||
         nb < 1) {
       cudaGetLastError();
       nb = 1;
@@ -426,7 +558,7 @@ StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) 
   q.bands = (g.nx + q.vw - 1) / q.vw;
   // one wave of units: as many runs per band as the resident warps allow,
   // each run at least 4M rows tall (its 2M-row overlap then costs <= 50%)
-  const long warps = (long)stream_occupancy(dt, q.depth) * stream_warps(dt) * std::max(sms, 1);
+  const long warps = (long)stream_occupancy(dt, q.depth, g.shape) * stream_warps(dt) * std::max(sms, 1);
   const int hmin = 4 * q.depth;
   int runs = (int)std::max<long>(1, warps / q.bands);
   runs = std::min(runs, std::max(1, g.ny / hmin));
@@ -458,8 +590,8 @@ cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const Gr
   p.ipath = ipath;
   p.nelem = (long)(g.ny + 2) * g.pitch;
   p.status = status;
-  for (int i = 0; i < 5; ++i) p.w[i] = g.w[i];
-  StreamFn fn = stream_fn(dt, q.depth, ipath, keep != nullptr);
+  for (int i = 0; i < 9; ++i) p.w[i] = g.w[i];
+  StreamFn fn = stream_fn(dt, q.depth, ipath, keep != nullptr, g.shape);
   if (!fn || m < 1 || m > q.depth) return cudaErrorInvalidValue;
   const long units = (long)q.bands * q.runs;
   const int W = stream_warps(dt);

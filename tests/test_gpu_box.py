@@ -56,7 +56,7 @@ def gpu_box(u0, w, steps, dtype="f64", algo="onestep", depth=None, wx=None, alia
 SIZES = [(1, 1), (1, 7), (7, 1), (5, 3), (63, 65), (130, 67), (257, 300)]
 
 
-@pytest.mark.parametrize("algo", ["onestep", "skewed"])
+@pytest.mark.parametrize("algo", ["onestep", "skewed", "stream"])
 @pytest.mark.parametrize("nx,ny", SIZES)
 def test_box_against_oracle_and_ring(algo, nx, ny):
     u0 = synth.field(nx, ny, 900 + nx + 7 * ny)
@@ -69,14 +69,14 @@ def test_box_against_oracle_and_ring(algo, nx, ny):
             assert np.array_equal(got[sl], u0[sl])
 
 
-@pytest.mark.parametrize("algo", ["onestep", "skewed"])
+@pytest.mark.parametrize("algo", ["onestep", "skewed", "stream"])
 def test_box_dyadic_bit_identical(algo):
     nx, ny = 100, 37
     u0 = synth.dyadic_field(nx, ny, 905)
     assert np.array_equal(gpu_box(u0, W_DYADIC, 6, algo=algo, depth=4), oracle.box_run(u0, W_DYADIC, 6))
 
 
-@pytest.mark.parametrize("algo", ["onestep", "skewed"])
+@pytest.mark.parametrize("algo", ["onestep", "skewed", "stream"])
 def test_box_in_place_alias(algo):
     nx, ny = 150, 90
     u0 = synth.field(nx, ny, 906)
@@ -101,7 +101,24 @@ def test_box_skewed_bitwise_equal_to_onestep(depth, wx, dtype):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("algo", ["onestep", "skewed"])
+@pytest.mark.parametrize("dtype,depth", [("f64", 2), ("f64", 3), ("f64", 4), ("f32", 4), ("f32", 6), ("f32", 8)])
+@pytest.mark.parametrize("nx,ny", [(700, 450), (1, 1), (5, 3), (3, 400), (129, 257)])
+def test_box_stream_bitwise_equal_to_onestep(dtype, depth, nx, ny):
+    """The stream schedule on the box: every depth it has a kernel for, step
+    counts below, at and across whole passes, in place and not."""
+    u0 = synth.field(nx, ny, 915 + nx)
+    w = box_weights(916)
+    if dtype == "f32":
+        u0 = u0.astype(np.float32)
+    for steps in sorted({1, depth - 1, depth, 2 * depth + 1, 13}):
+        if steps < 1:
+            continue
+        ref = gpu_box(u0, w, steps, dtype=dtype, algo="onestep")
+        assert np.array_equal(gpu_box(u0, w, steps, dtype=dtype, algo="stream", depth=depth), ref), (steps,)
+        assert np.array_equal(gpu_box(u0, w, steps, dtype=dtype, algo="stream", depth=depth, alias=True), ref)
+
+
+@pytest.mark.parametrize("algo", ["onestep", "skewed", "stream"])
 def test_box_f32_against_f32_and_f64_oracles(algo):
     nx, ny, steps = 333, 211, 40
     u0 = synth.field(nx, ny, 920)
@@ -135,7 +152,7 @@ def test_box_autotune(monkeypatch):
     p = j2d5pt.Plan.box9(nx, ny, "f64", w)
     src, dst = p.to_device(u0), p.empty()
     desc = p.autotune(src, dst, steps)
-    assert "algo=onestep" in desc or "algo=skewed" in desc
+    assert "algo=onestep" in desc or "algo=skewed" in desc or "algo=stream" in desc
     dst.zero_()
     p.run(src, dst, steps)
     p.sync()
@@ -210,7 +227,7 @@ def test_box_cells_bit_exact(fname, int_path):
     ref = u0
     for _ in range(steps):
         ref = model_box_step(ref, w, mask, guard)
-    for algo in ("onestep", "skewed"):
+    for algo in ("onestep", "skewed", "stream"):
         got = gpu_box(u0, w, steps, algo=algo, depth=steps, int_path=int_path)
         bad = np.argwhere(got != ref)
         assert bad.size == 0, "%s/%s/int_path=%d: %d cells differ, first %s" % (algo, fname, int_path, len(bad),
