@@ -79,9 +79,10 @@ typedef enum {
                             (step t of row i-t as row i arrives); one launch per pass, no shared
                             memory.  k in {4, 6, 8, 10, 12} for FP32, {2, 3, 4, 6} for FP64
                             (J2D_ERR_ARG otherwise; default 8 and 2); box plans: {4, 6, 8} for
-                            FP32, {2, 3, 4} for FP64 (default 4 and 2).  Forward runs of single
+                            FP32, {2, 3, 4} for FP64 (default 8 and 2).  Forward runs of single
                             grids only (adjoint runs and batches take TILES).  AUTO takes it for
-                            FP32 grids too large for the chip. */
+                            FP32 grids too large for the chip and FP64 grids of 8192^2 cells or
+                            more. */
 } j2d_algo;
 
 /* Plan options (j2d5pt_set_option / j2d5pt_get_option). */
@@ -133,7 +134,7 @@ j2d_status j2d5pt_plan_batched(j2d5pt_plan_t *plan, int count, const int *nx, co
  * describe, timing and status calls; its algorithms are J2D_ALGO_ONESTEP,
  * J2D_ALGO_SKEWED and J2D_ALGO_STREAM (any other choice runs the skewed
  * tiles; AUTO takes the stream schedule for FP32 grids too large for the
- * chip).  The adjoint,
+ * chip and FP64 grids of 8192^2 cells or more).  The adjoint,
  * weight-gradient and j2d5pt_set_weights calls return J2D_ERR_UNSUPPORTED.
  * FP64 cells are evaluated as j2d5pt_arith_info describes, with the nine
  * terms: the FMA chain takes the product of the (y-1, x) term, then the

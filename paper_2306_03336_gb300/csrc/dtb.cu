@@ -1869,10 +1869,12 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
   if (algo == J2D_ALGO_AUTO) {
     if (rq.steps < 4) algo = J2D_ALGO_ONESTEP;
     else if (fits && (single || dt == J2D_F64)) algo = J2D_ALGO_RESIDENT;  // FP64 batches: grouped resident
-    // FP32 grids too large for the chip: the stream schedule (16384^2: 3820
-    // GCells/s against 1950 for the best shared-memory schedule; the box 2397
-    // against 1418)
-    else if (single && dt == J2D_F32 && !rq.adjoint) algo = J2D_ALGO_STREAM;
+    // grids too large for the chip: the stream schedule for FP32 (16384^2:
+    // 4254 GCells/s against 1950 for the best shared-memory schedule; the box
+    // 2578 against 1418) and for large FP64 grids (16384^2: 194 against 162 for
+    // the tiles; 8192^2: 170; at 4096^2 the tiles are faster, 143 against 130)
+    else if (single && !rq.adjoint && (dt == J2D_F32 || (long)grids[0].nx * grids[0].ny >= (8192L << 13)))
+      algo = J2D_ALGO_STREAM;
     else algo = J2D_ALGO_TILES;
   }
   if (algo == J2D_ALGO_RESIDENT && !fits) algo = single ? J2D_ALGO_BANDS : J2D_ALGO_TILES;
@@ -1891,7 +1893,7 @@ DtbConfig dtb_choose(j2d_dtype dt, const std::vector<GridDesc> &grids, int sms, 
     c.sweep = 2;
     c.rows = dtb_rows_max_pair(dt, smem_optin);
   }
-  if (algo == J2D_ALGO_STREAM && rq.depth <= 0) c.depth = dt == J2D_F64 ? 2 : (grids[0].shape == 9 ? 4 : 8);
+  if (algo == J2D_ALGO_STREAM && rq.depth <= 0) c.depth = dt == J2D_F64 ? 2 : 8;
   if (algo == J2D_ALGO_SKEWED) {
     c.rows = dtb_rows_max_skew(dt, smem_optin);
     if (rq.depth <= 0) c.depth = dt == J2D_F64 ? 8 : 16;

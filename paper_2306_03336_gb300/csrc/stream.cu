@@ -556,11 +556,15 @@ StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) 
   q.G = (q.depth + V - 1) / V * V;
   q.vw = 32 * V - 2 * q.G;
   q.bands = (g.nx + q.vw - 1) / q.vw;
-  // one wave of units: as many runs per band as the resident warps allow,
-  // each run at least 4M rows tall (its 2M-row overlap then costs <= 50%)
+  // Several waves of units per pass, so that the block scheduler balances
+  // the SMs as units finish (FP64 k = 2 on 16384^2: 159 GCells/s with one
+  // wave of units, 178 / 191 / 194 / 189 / 175 with 2 / 4 / 8 / 16 / 32;
+  // FP32 k = 8: 3958, 4254 with 2 or 3, 4235 with 4, 4090 with 8), each run
+  // at least 32M rows tall (its 2M-row overlap then costs at most 6%).
   const long warps = (long)stream_occupancy(dt, q.depth, g.shape) * stream_warps(dt) * std::max(sms, 1);
-  const int hmin = 4 * q.depth;
-  int runs = (int)std::max<long>(1, warps / q.bands);
+  const int waves = dt == J2D_F64 ? 8 : 3;
+  const int hmin = 32 * q.depth;
+  int runs = (int)std::max<long>(1, waves * warps / q.bands);
   runs = std::min(runs, std::max(1, g.ny / hmin));
   q.H = (g.ny + runs - 1) / runs;
   q.runs = (g.ny + q.H - 1) / q.H;
