@@ -684,7 +684,7 @@ WORKLOADS = {
     "f32onestep": (8192, 8192, "f32", "onestep", 0, 0, 4, 1),
     "f32stream": (8192, 8192, "f32", "stream", 8, 0, 16, 1),
     "f64stream": (8192, 8192, "f64", "stream", 2, 0, 4, 1),
-    "f32boxstream": (8192, 8192, "f32", "box:stream", 4, 0, 8, 1),
+    "f32boxstream": (8192, 8192, "f32", "box:stream", 8, 0, 16, 1),
     "f64box": (8192, 8192, "f64", "box:skewed", 4, 4, 8, 1),
     "f64batch": (64, 0, "f64", "batch:resident", 0, 0, 20, 1),
 }
