@@ -4,7 +4,8 @@
 // 3.3, Figure 1) keeps a tile on chip for several time steps so that one trip
 // through HBM carries many steps.  On GB300 the register file (256 KB per SM)
 // is larger than shared memory (228 KB), so this schedule keeps the time steps
-// of a tile in registers and uses no shared memory at all.
+// of a tile in registers; shared memory only stages the input rows on their
+// way in (a ring of a few rows per warp, filled by asynchronous copies).
 //
 // Each warp owns one column band of the grid, 32 lanes x one 16-byte vector
 // (128 FP32 / 64 FP64 columns), and a run of rows, and sweeps the run from top
@@ -32,8 +33,11 @@
 // So the results are bit-identical to every other kernel of the library.
 //
 // One launch per pass (the passes of a run are ordered on the stream; a run of
-// S steps is ceil(S / M) passes, the first one taking the remainder).  Per cell
-// update HBM carries 2 * sizeof(T) * (1 + overlap) / M bytes.
+// S steps is ceil(S / M) passes, the first one taking the remainder), with
+// several waves of (band, run) units so that the block scheduler balances the
+// SMs.  Per cell update HBM carries 2 * sizeof(T) * (1 + overlap) / M bytes.
+// The same pipeline serves the 3x3 box (j2d9pt) and, for state-keeping runs,
+// stores every step's rows instead of the last step's only.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -84,10 +88,6 @@ struct WeightsF {
 };
 
 __device__ __forceinline__ RowF row_zero(RowF *) { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
-__device__ __forceinline__ RowF row_load(const float *p, RowF *) {
-  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-  return {make_float2(v.x, v.z), make_float2(v.y, v.w)};
-}
 __device__ __forceinline__ void row_store(float *p, const RowF &r) {
   *reinterpret_cast<float4 *>(p) = make_float4(r.a.x, r.b.x, r.a.y, r.b.y);
 }
@@ -133,10 +133,6 @@ struct WeightsD {
 };
 
 __device__ __forceinline__ RowD row_zero(RowD *) { return {0.0, 0.0}; }
-__device__ __forceinline__ RowD row_load(const double *p, RowD *) {
-  const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-  return {v.x, v.y};
-}
 __device__ __forceinline__ void row_store(double *p, const RowD &r) {
   *reinterpret_cast<double2 *>(p) = make_double2(r.a, r.b);
 }
@@ -560,10 +556,12 @@ StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) 
   // the SMs as units finish (FP64 k = 2 on 16384^2: 159 GCells/s with one
   // wave of units, 178 / 191 / 194 / 189 / 175 with 2 / 4 / 8 / 16 / 32;
   // FP32 k = 8: 3958, 4254 with 2 or 3, 4235 with 4, 4090 with 8), each run
-  // at least 32M rows tall (its 2M-row overlap then costs at most 6%).
+  // at least 32M (FP64) or 16M (FP32) rows tall, its 2M-row overlap then
+  // costing at most 6% or 12% (FP64 8192^2: 169.7 GCells/s against 164.8 with
+  // 16M; FP32 4096^2: 2764 against 2175 with 32M).
   const long warps = (long)stream_occupancy(dt, q.depth, g.shape) * stream_warps(dt) * std::max(sms, 1);
   const int waves = dt == J2D_F64 ? 8 : 3;
-  const int hmin = 32 * q.depth;
+  const int hmin = (dt == J2D_F64 ? 32 : 16) * q.depth;
   int runs = (int)std::max<long>(1, waves * warps / q.bands);
   runs = std::min(runs, std::max(1, g.ny / hmin));
   q.H = (g.ny + runs - 1) / runs;
