@@ -99,3 +99,21 @@ def test_plan_without_gpu_reports_device_error(lib):
     st = lib.j2d5pt_plan(ctypes.byref(h), 8, 8, 0, w.ctypes.data_as(ctypes.c_void_p))
     assert st == j2d5pt.J2D_ERR_DEVICE
     assert h.value is None
+
+
+def _header_enum(prefix):
+    """name -> value of the header's enumerators that start with prefix."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(%s[A-Z0-9_]+)\s*=\s*(\d+)" % prefix, src)}
+
+
+def test_binding_enums_match_the_header():
+    """The binding passes algorithms, options and status codes by the
+    header's values (it marshals names to the C enumerators)."""
+    algos = _header_enum("J2D_ALGO_")
+    assert {("J2D_ALGO_" + k.upper()): v for k, v in j2d5pt.ALGO.items()} == algos
+    opts = _header_enum("J2D_OPT_")
+    assert {("J2D_OPT_" + k.upper()): v for k, v in j2d5pt.OPT.items()} == opts
+    for name, v in _header_enum("J2D_ERR_").items():
+        assert getattr(j2d5pt, name) == v, name
+    assert algos["J2D_ALGO_STREAM"] == 6
