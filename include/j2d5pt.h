@@ -300,6 +300,20 @@ j2d_status j2d9pt_measure_exact_rate(double *cells_per_s);
  * same roles).  Either pointer may be NULL.  Never fails. */
 j2d_status j2d5pt_arith_info(unsigned *exact_mask, int *exact_guard);
 
+/* Geometry of the stream schedule (J2D_ALGO_STREAM) for an nx x ny grid of
+ * the given dtype and shape (5: five-point, 9: the 3x3 box) at `depth` steps
+ * per pass, when the device holds `resident_warps` warps of the stream kernel
+ * at once (a plan takes that from the kernel's occupancy and the SM count).
+ * Host arithmetic only, no device call.  out[0..5] = {steps per pass k, halo
+ * columns G on each side of a band (k rounded up to a whole 16-byte vector),
+ * stored columns per band (32 vectors' worth minus 2G), bands
+ * (ceil(nx / stored columns)), rows stored per run H, runs per band}: band b
+ * stores columns [1 + b*(stored), ...) and run r rows [1 + r*H, ...), each
+ * clipped to the grid.  J2D_ERR_ARG for sizes < 1, an unknown dtype or shape,
+ * a depth with no stream kernel, resident_warps < 1 or a NULL out. */
+j2d_status j2d5pt_stream_geometry(int nx, int ny, j2d_dtype dtype, int shape, int depth, long resident_warps,
+                                  long out[6]);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all plans); a diagnostic for launch accounting. */
 long j2d5pt_kernel_launches(void);

@@ -886,6 +886,25 @@ extern "C" j2d_status j2d9pt_measure_exact_rate(double *cells_per_s) {
   return J2D_OK;
 }
 
+extern "C" j2d_status j2d5pt_stream_geometry(int nx, int ny, j2d_dtype dtype, int shape, int depth, long resident_warps,
+                                             long out[6]) {
+  if (nx < 1 || ny < 1) return fail(J2D_ERR_ARG, "stream_geometry: nx=%d ny=%d (need >= 1)", nx, ny);
+  if (dtype != J2D_F64 && dtype != J2D_F32) return fail(J2D_ERR_ARG, "stream_geometry: unknown dtype %d", (int)dtype);
+  if (shape != 5 && shape != 9) return fail(J2D_ERR_ARG, "stream_geometry: shape %d (5 or 9)", shape);
+  if (!out) return fail(J2D_ERR_ARG, "stream_geometry: null output");
+  if (resident_warps < 1) return fail(J2D_ERR_ARG, "stream_geometry: resident_warps %ld < 1", resident_warps);
+  if (!stream_depth_ok(dtype, depth, shape))
+    return fail(J2D_ERR_ARG, "stream_geometry: no stream kernel of depth %d for this dtype and shape", depth);
+  const StreamGeom q = stream_geometry_warps(dtype, nx, ny, depth, resident_warps);
+  out[0] = q.depth;
+  out[1] = q.G;
+  out[2] = q.vw;
+  out[3] = q.bands;
+  out[4] = q.H;
+  out[5] = q.runs;
+  return J2D_OK;
+}
+
 extern "C" j2d_status j2d5pt_arith_info(unsigned *exact_mask, int *exact_guard) {
   if (exact_mask) *exact_mask = kExactMask;
   if (exact_guard) *exact_guard = kExactGuard;

@@ -87,6 +87,8 @@ int stream_max_depth(j2d_dtype dt);
 bool stream_depth_ok(j2d_dtype dt, int m, int shape = 5);  // a kernel of m steps per pass exists
 bool stream_keep_ok(j2d_dtype dt, int m);   // ... and one that keeps every state
 StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms);
+// The same for a given number of warps resident at once (host arithmetic only).
+StreamGeom stream_geometry_warps(j2d_dtype dt, int nx, int ny, int depth, long warps);
 cudaError_t launch_stream_pass(j2d_dtype dt, const void *in, void *out, const GridDesc &g, const StreamGeom &q, int m,
                                int ipath, int *status, cudaStream_t s, void *keep = nullptr, long keep_stride = 0);
 

@@ -546,12 +546,18 @@ static int stream_occupancy(j2d_dtype dt, int m, int shape) {
 }
 
 StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) {
+  const int d = std::max(1, std::min(depth, stream_max_depth(dt)));
+  const long warps = (long)stream_occupancy(dt, d, g.shape) * stream_warps(dt) * std::max(sms, 1);
+  return stream_geometry_warps(dt, g.nx, g.ny, depth, warps);
+}
+
+StreamGeom stream_geometry_warps(j2d_dtype dt, int nx, int ny, int depth, long warps) {
   StreamGeom q;
   const int V = dt == J2D_F64 ? 2 : 4;
   q.depth = std::max(1, std::min(depth, stream_max_depth(dt)));
   q.G = (q.depth + V - 1) / V * V;
   q.vw = 32 * V - 2 * q.G;
-  q.bands = (g.nx + q.vw - 1) / q.vw;
+  q.bands = (nx + q.vw - 1) / q.vw;
   // Several waves of units per pass, so that the block scheduler balances
   // the SMs as units finish (FP64 k = 2 on 16384^2: 159 GCells/s with one
   // wave of units, 178 / 191 / 194 / 189 / 175 with 2 / 4 / 8 / 16 / 32;
@@ -559,13 +565,13 @@ StreamGeom stream_geometry(j2d_dtype dt, const GridDesc &g, int depth, int sms) 
   // at least 32M (FP64) or 16M (FP32) rows tall, its 2M-row overlap then
   // costing at most 6% or 12% (FP64 8192^2: 169.7 GCells/s against 164.8 with
   // 16M; FP32 4096^2: 2764 against 2175 with 32M).
-  const long warps = (long)stream_occupancy(dt, q.depth, g.shape) * stream_warps(dt) * std::max(sms, 1);
+  warps = std::max(warps, 1L);
   const int waves = dt == J2D_F64 ? 8 : 3;
   const int hmin = (dt == J2D_F64 ? 32 : 16) * q.depth;
   int runs = (int)std::max<long>(1, waves * warps / q.bands);
-  runs = std::min(runs, std::max(1, g.ny / hmin));
-  q.H = (g.ny + runs - 1) / runs;
-  q.runs = (g.ny + q.H - 1) / q.H;
+  runs = std::min(runs, std::max(1, ny / hmin));
+  q.H = (ny + runs - 1) / runs;
+  q.runs = (ny + q.H - 1) / q.H;
   return q;
 }
 

@@ -89,6 +89,7 @@ def _open(path):
         "j2d5pt_measure_exact_rate": [ctypes.POINTER(D)],
         "j2d5pt_measure_smem_bandwidth": [ctypes.POINTER(D)],
         "j2d5pt_arith_info": [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(I)],
+        "j2d5pt_stream_geometry": [I, I, I, I, I, L, ctypes.POINTER(L)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -281,6 +282,16 @@ def j2d5pt_arith_info():
     m, g = ctypes.c_uint(), ctypes.c_int()
     _check(load().j2d5pt_arith_info(ctypes.byref(m), ctypes.byref(g)))
     return int(m.value), int(g.value)
+
+
+def j2d5pt_stream_geometry(nx, ny, dtype, depth, resident_warps, shape=5):
+    """The stream schedule's geometry (host arithmetic): a dict with the steps
+    per pass, halo columns G, stored columns per band, bands, rows per run H
+    and runs per band."""
+    out = (ctypes.c_long * 6)()
+    _check(load().j2d5pt_stream_geometry(int(nx), int(ny), _DT[dtype], int(shape), int(depth), int(resident_warps),
+                                         out))
+    return dict(zip(("depth", "G", "vw", "bands", "H", "runs"), (int(v) for v in out)))
 
 
 _DT = {"f64": J2D_F64, "f32": J2D_F32, np.float64: J2D_F64, np.float32: J2D_F32}

@@ -117,3 +117,46 @@ def test_binding_enums_match_the_header():
     for name, v in _header_enum("J2D_ERR_").items():
         assert getattr(j2d5pt, name) == v, name
     assert algos["J2D_ALGO_STREAM"] == 6
+
+
+def test_stream_geometry_covers_the_grid(lib):
+    """The stream schedule's bands and runs (host arithmetic, no device):
+    every interior cell is stored by exactly one (band, run) unit, each
+    band's stored columns start on a 16-byte vector and lie at least G >= k
+    columns inside the 32 vectors it evaluates, and runs are as tall as the
+    minimum the schedule keeps (or the whole grid)."""
+    rng = np.random.Generator(np.random.PCG64(2306034900))
+    cases = [(16384, 16384, "f64", 2, 3648), (16384, 16384, "f32", 8, 1824), (1, 1, "f64", 4, 1),
+             (8592, 8328, "f32", 12, 1520), (3, 700, "f32", 4, 4000), (700, 3, "f64", 6, 100)]
+    for _ in range(60):
+        dt = str(rng.choice(["f64", "f32"]))
+        depth = int(rng.choice([2, 3, 4, 6] if dt == "f64" else [4, 6, 8, 10, 12]))
+        cases.append((int(rng.integers(1, 20000)), int(rng.integers(1, 20000)), dt, depth, int(rng.integers(1, 5000))))
+    for nx, ny, dt, depth, warps in cases:
+        q = j2d5pt.j2d5pt_stream_geometry(nx, ny, dt, depth, warps)
+        V = 2 if dt == "f64" else 4
+        off = V - 1  # the plan layout's element offset of column 0
+        assert q["depth"] == depth and q["G"] >= depth and q["G"] % V == 0
+        assert q["vw"] == 32 * V - 2 * q["G"] > 0
+        cols = np.zeros(nx + 2, dtype=np.int64)
+        for b in range(q["bands"]):
+            lo, hi = 1 + b * q["vw"], min(1 + (b + 1) * q["vw"], nx + 1)
+            assert lo <= nx
+            assert (off + lo) % V == 0  # the first stored vector is aligned
+            cols[lo:hi] += 1
+        assert (cols[1:nx + 1] == 1).all() and cols[0] == 0 and cols[nx + 1] == 0, (nx, dt, depth)
+        rows = np.zeros(ny + 2, dtype=np.int64)
+        for r in range(q["runs"]):
+            lo, hi = 1 + r * q["H"], min(1 + (r + 1) * q["H"], ny + 1)
+            assert lo <= ny
+            rows[lo:hi] += 1
+        assert (rows[1:ny + 1] == 1).all(), (ny, q)
+        hmin = (32 if dt == "f64" else 16) * depth
+        assert q["runs"] == 1 or q["H"] >= hmin or ny < hmin, (ny, q)
+    # the box has its own depths; argument errors are refused before any device call
+    assert j2d5pt.j2d5pt_stream_geometry(1000, 1000, "f32", 8, 100, shape=9)["G"] == 8
+    for bad in [(0, 5, "f64", 2, 10, 5), (5, 5, "f64", 5, 10, 5), (5, 5, "f32", 2, 10, 5), (5, 5, "f64", 2, 0, 5),
+                (5, 5, "f64", 6, 10, 9)]:
+        with pytest.raises(j2d5pt.J2DError) as e:
+            j2d5pt.j2d5pt_stream_geometry(*bad[:5], shape=bad[5])
+        assert e.value.status == j2d5pt.J2D_ERR_ARG
